@@ -1,0 +1,241 @@
+/*
+ * libmg: GB300 (sm_103a) FAS multigrid solver for the DGP brane-bending mode.
+ *
+ * The equation (arXiv:1303.0008, Eq. code_eqn in code units, box length 1, mean
+ * density 1) is written here as
+ *
+ *     lap(phi) + alpha [ (lap phi)^2 - (grad_i grad_j phi)^2 ] = kappa * delta
+ *
+ * so alpha = R_c^2 / (3 beta a^4) (the paper's own alpha is 1/alpha) and
+ * kappa = Omega_m a / beta.  It is discretised as in Sec. III.B (7-point
+ * Laplacian, four-point cross differences: a 19-point stencil), split with
+ * w = 1/3 and solved for the root of Eq. two_branch; the smoother takes one
+ * Newton step per cell (Sec. III.B) in a four-colour Gauss-Seidel order, inside
+ * FAS V-cycles (Sec. III.C): residual, full-weighting restriction, the coarse
+ * equation L^H(phi^H) = L^H(R phi^h) - R d^h, trilinear prolongation of the
+ * correction.  Refinement levels take Dirichlet values interpolated from the
+ * level below (Sec. III.C, first paragraph; Sec. IV.D).
+ *
+ * Conventions of every call:
+ *   - A status code is returned; nothing throws across this boundary.
+ *     mg_last_error() gives a message for the calling thread.
+ *   - Arrays are float64, x fastest: a[i + n*(j + n*k)].  A patch array is
+ *     [count][8][8][8] in the same order within each patch.
+ *   - on_device = 1: the pointer is device memory of the current device and the
+ *     copy is ordered on the handle's stream; on_device = 0: host memory, and the
+ *     call returns when the copy is complete.
+ *   - Inputs are copied, never retained.  Outputs go to caller-owned buffers.
+ *   - The handle owns all of its device memory; calls on one handle are not
+ *     thread-safe.
+ *   - Periodic grids solve the bordered system L^h phi = lambda with
+ *     mean(phi) = 0: the discrete nonlinear term does not sum to zero over a
+ *     periodic box, and the constant lambda (reported in the statistics) takes up
+ *     the difference.  The residual reported and tested against `tol` is
+ *     max |d - lambda|, d = L^h phi.
+ *   - The square root of Eq. two_branch is taken of max(q, 0): where the
+ *     discriminant is negative the root is its real part, and the cell is counted
+ *     in guard_hits.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_grid mg_grid;
+
+typedef enum {
+  MG_OK = 0,
+  MG_EINVAL = 1,   /* bad argument (size, level, patch index, branch, pointer) */
+  MG_ENOMEM = 2,   /* device or host allocation failed */
+  MG_ECUDA = 3,    /* a CUDA call failed; see mg_last_error() */
+  MG_ENOCONV = 4,  /* max_cycles reached, residual grew 1e3-fold, or stalled */
+  MG_ENAN = 5,     /* a residual was not finite */
+  MG_ETIMEOUT = 6, /* a device-side wait ran out (reserved) */
+  MG_ESTATE = 7    /* call out of order (e.g. solve before set_density) */
+} mg_status;
+
+typedef enum {
+  MG_FP64 = 0,  /* every step in FP64 */
+  MG_MIXED = 1  /* FP32 correction V-cycles inside an FP64 defect-correction loop */
+} mg_precision;
+
+/*
+ * What to do where the square root of Eq. two_branch would be imaginary.  The
+ * operator splitting of Sec. III.A keeps the discriminant non-negative for any
+ * field as long as 1 + 4(1-w) alpha kappa delta >= 0 in every cell; beyond that
+ * (alpha*kappa > 3/8 in voids) the equation has no real local root.
+ *   MG_GUARD_FLOOR (default): the source is held at that bound,
+ *     kappa*delta -> the value with 1 + 4(1-w) alpha kappa delta = 0, so no root is
+ *     ever imaginary; guard_hits counts the floored cells of the finest level.
+ *   MG_GUARD_ROOT: the square root is taken of max(q, 0) (the real part of the
+ *     complex root); guard_hits counts the cells where q < 0.  Far beyond the
+ *     bound the Newton-Gauss-Seidel iteration can cycle instead of converging.
+ * Both are the same system when every cell satisfies the bound.
+ */
+typedef enum {
+  MG_GUARD_FLOOR = 0,
+  MG_GUARD_ROOT = 1
+} mg_guard;
+
+typedef struct {
+  mg_precision prec;
+  int nu_pre;        /* pre-smoothing sweeps per level (default 2) */
+  int nu_post;       /* post-smoothing sweeps per level (default 2) */
+  int coarsest;      /* stop coarsening at this many cells per side or fewer (default 4) */
+  int max_cycles;    /* V-cycles (FP64) or outer corrections (mixed); default 100 */
+  int inner_cycles;  /* mixed: FP32 V-cycles per FP64 correction (default 3) */
+  int use_graphs;    /* capture each V-cycle in a CUDA graph (default 1) */
+  int coarse_sweeps; /* cap on coarsest-level sweeps (default 200) */
+  double coarse_drop;/* coarsest solve stops when its residual fell by this (1e-6) */
+  int time_kernels;  /* 1: time every launch of the finest-level smoother with CUDA
+                        events on the handle's stream (stats.kernel_ms); default 0 */
+  mg_guard guard;    /* default MG_GUARD_FLOOR */
+  int patch_coarse_sweeps; /* sweeps on the coarsest (2^3 per patch) level of a
+                              refinement union per V-cycle (default 8) */
+} mg_options;
+
+typedef struct {
+  int cycles;          /* V-cycles (FP64) or total inner V-cycles (mixed) */
+  int outer;           /* FP64 residual evaluations (mixed) */
+  int status;          /* the mg_status of the solve */
+  int levels;          /* multigrid levels used */
+  double res0;         /* residual at the first check */
+  double res;          /* final max |d - lambda| */
+  double lambda;       /* compatibility constant (periodic) */
+  double wall_s;       /* device time of the solve */
+  long long guard_hits;/* finest-level cells floored (MG_GUARD_FLOOR) or with a negative
+                          discriminant at the last check (MG_GUARD_ROOT) */
+  int hist_len;
+  double res_hist[128];/* residual at each check */
+  long long launches;  /* kernels launched by the solve (graph nodes included) */
+  long long kernel_launches; /* finest-level smoother launches timed (time_kernels) */
+  double kernel_ms;    /* their summed device time in milliseconds */
+  double kernel_cells; /* cell updates those launches performed */
+} mg_solve_stats;
+
+/* Fill `opt` with the defaults listed above. */
+void mg_default_options(mg_options* opt);
+
+/*
+ * Create a periodic n^3 domain grid (n even, 4 <= n <= 2048).  `opt` may be NULL
+ * (defaults).  Allocates the level hierarchy n, n/2, ... down to `coarsest`
+ * (halving while the half is even and at least 4) on the current device.
+ * Errors: MG_EINVAL for a bad n or options, MG_ENOMEM, MG_ECUDA.
+ */
+mg_status mg_create_grid(mg_grid** out, int n, const mg_options* opt);
+
+/* Order the handle's work on `stream` (a cudaStream_t; NULL = the handle's own
+ * non-blocking stream, the default).  The stream must outlive its use. */
+mg_status mg_set_stream(mg_grid* g, void* stream);
+
+/*
+ * Add `count` 8^3 refinement patches to level `level` (1 or 2; level 1 needs the
+ * domain, level 2 needs level 1 in place).  origin[3*p..3*p+2] = (x, y, z) of
+ * patch p in level cells (cell size 1/(n 2^level)), each a multiple of 8 and in
+ * [0, n 2^level).  Patches of one level must not overlap; the level's parent
+ * cells dilated by one cell must lie in level-1 patches (proper nesting, checked
+ * when level 2 is solved).  Replaces any patches the level had.
+ * Errors: MG_EINVAL (alignment, range, duplicates), MG_ENOMEM, MG_ECUDA.
+ */
+mg_status mg_add_patches(mg_grid* g, int level, int count, const int32_t* origin);
+
+/*
+ * Set the density contrast delta = rho - 1 (Eq. code_eqn).  level 0 with patch = -1:
+ * the n^3 domain array (restricted to every coarse level here).  level >= 1 with
+ * patch = -1: all patches of the level, [count][8][8][8]; patch >= 0: one patch.
+ * For a batch handle (mg_create_batch) `level` must be 0 and `patch` selects
+ * the solve.  Errors: MG_EINVAL, MG_ECUDA.
+ */
+mg_status mg_set_density(mg_grid* g, int level, int patch, const double* delta, int on_device);
+
+/* Set the field phi (initial guess, or a saved state to resume from); same
+ * addressing as mg_set_density.  The field starts at zero otherwise. */
+mg_status mg_set_field(mg_grid* g, int level, int patch, const double* phi, int on_device);
+
+/*
+ * Solve every level of the grid: the domain by FAS V-cycles until
+ * max|d - lambda| < tol, then each refinement level in turn with its Dirichlet
+ * fill taken from the solved level below, until max|d| < tol.  `branch` is the
+ * sign in front of the square root of Eq. two_branch (+1 or -1); 0 selects
+ * sgn(alpha), the physical root of Eq. one_branch.  With alpha = 0 the equation
+ * is the linear Poisson equation and branch must be 0.  tol is in the units of
+ * kappa*delta.  `stats` may be NULL; it describes the domain solve.
+ * On MG_ENOCONV or MG_ENAN the last iterate stays in the handle.
+ * Errors: MG_EINVAL, MG_ESTATE (no density), MG_ENOCONV, MG_ENAN, MG_ECUDA.
+ */
+mg_status mg_solve(mg_grid* g, int branch, double alpha, double kappa, double tol,
+                   mg_solve_stats* stats);
+
+/* Copy the field out (same addressing as mg_set_density). */
+mg_status mg_get_field(const mg_grid* g, int level, int patch, double* out, int on_device);
+
+/*
+ * The fifth force g = -(1/2) grad(phi) (Sec. II.B) by central differences
+ * (Sec. III.B), as 3 x cells float64 (x components, then y, then z).  Level 0:
+ * 3 x n^3.  Level >= 1: 3 x count x 512 for patch = -1, 3 x 512 for one patch;
+ * differences at patch faces use the neighbouring patch or the Dirichlet fill.
+ */
+mg_status mg_get_force(const mg_grid* g, int level, int patch, double* out, int on_device);
+
+/* Release the handle and all of its device memory.  NULL is ignored. */
+void mg_destroy_grid(mg_grid* g);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* mg_last_error(void);
+
+/*
+ * Batched independent periodic solves (one handle, `count` grids of sides n[s],
+ * each valid for mg_create_grid).  Densities and fields are set per solve with
+ * mg_set_density / mg_set_field (level 0, patch = solve index).
+ */
+mg_status mg_create_batch(mg_grid** out, int count, const int* n, const mg_options* opt);
+
+/*
+ * Solve every grid of a batch handle to max|d - lambda| < tol.  branch, alpha and
+ * kappa hold one entry per solve; `stats` (may be NULL) holds `count` entries.
+ * Returns MG_OK when every solve converged, else the first failing status.
+ */
+mg_status mg_solve_batch(mg_grid* g, const int* branch, const double* alpha, const double* kappa,
+                         double tol, mg_solve_stats* stats);
+
+/* ------------------------------------------------------------------------
+ * Single-kernel entry points on caller-owned device arrays (periodic n^3,
+ * float64, x fastest), ordered on `stream` (a cudaStream_t, NULL = legacy
+ * default stream).  They run the same kernels as mg_solve and exist so that
+ * each step can be checked on its own.  Errors: MG_EINVAL, MG_ENOMEM, MG_ECUDA.
+ * ---------------------------------------------------------------------- */
+
+/*
+ * d = L^h phi - f (Sec. III.C residual; L^h of Sec. III.B), h = 1/n.  f may be
+ * NULL (f = 0); d may be NULL (norms only).  norms (host, 5 doubles, may be
+ * NULL): [sum d, max d, min d, guarded cells, non-finite cells].  Synchronises
+ * the stream when norms is given.
+ */
+mg_status mg_op_residual(int n, const double* phi, const double* delta, const double* f,
+                         int branch, double alpha, double kappa, double* d, double* norms,
+                         void* stream);
+
+/* `sweeps` four-colour Newton-Gauss-Seidel sweeps of L^h phi = f + lambda in place
+ * (f may be NULL). */
+mg_status mg_op_smooth(int n, double* phi, const double* delta, const double* f, int branch,
+                       double alpha, double kappa, double lambda, int sweeps, void* stream);
+
+/* coarse[(n/2)^3] = mean of the 8 children of fine[n^3] (n even). */
+mg_status mg_op_restrict(int n, const double* fine, double* coarse, void* stream);
+
+/* fine[n^3] += P(coarse - coarse_ref), trilinear, coarse arrays (n/2)^3. */
+mg_status mg_op_prolong_correct(int n, const double* coarse, const double* coarse_ref,
+                                double* fine, void* stream);
+
+/* out[3 n^3] = -(1/2) grad phi. */
+mg_status mg_op_force(int n, const double* phi, double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_H */

@@ -174,6 +174,28 @@ static void orc_sweep_periodic(int n, double h, double* phi, const double* delta
       }
 }
 
+/*
+ * Source floor (a reading of Sec. III.A): the operator splitting keeps the
+ * discriminant alpha^2 + 4(1-w) Sigma of Eq. two_branch non-negative for any field
+ * as long as its source part alpha^2 + 4(1-w) alpha kappa delta is, i.e.
+ * 1 + 4(1-w) alpha_B kappa delta >= 0.  Cells below that bound get the delta that
+ * meets it with equality.  out may alias delta.  Returns the cells changed.
+ */
+long orc_density_floor(long cells, const double* delta, double alpha_B, double kappa,
+                       double w, double* out) {
+  const double t = 4.0 * (1.0 - w) * alpha_B * kappa;
+  long hits = 0;
+  for (long c = 0; c < cells; ++c) {
+    double v = delta[c];
+    if (t != 0.0 && 1.0 + t * v < 0.0) {
+      v = -1.0 / t;
+      ++hits;
+    }
+    out[c] = v;
+  }
+  return hits;
+}
+
 /* Cell-centred full weighting: the mean of the 8 children (reading of the
  * restriction operator R of Sec. III.C).  nc = coarse cells per side. */
 void orc_restrict(int nc, const double* fine, double* coarse) {
@@ -608,8 +630,8 @@ long orc_patch_residual(int n0, int level, int count, const int32_t* org,
 
 /*
  * Solve a refinement level: lexicographic Newton-Gauss-Seidel over the patches
- * (in list order, cells in lexicographic order) until max|d| < tol or
- * max_sweeps.  phi holds the initial guess on entry.
+ * (in list order, cells in lexicographic order) until max|d| < tol (tested every
+ * 10 sweeps) or max_sweeps.  phi holds the initial guess on entry.
  * stats (may be NULL): [0] sweeps [1] residual [2] guarded cells [3] status.
  */
 int orc_patch_solve(int n0, int level, int count, const int32_t* org,
@@ -623,25 +645,15 @@ int orc_patch_solve(int n0, int level, int count, const int32_t* org,
   if (st) { orc_reflevel_free(&rl); return st; }
   orc_params p = {alpha_B, kappa, w, branch};
   double h = 1.0 / (double)(n0 << level);
-  long total = (long)count * ORC_PC;
-  double* d = (double*)malloc(sizeof(double) * (size_t)(total > 0 ? total : 1));
   double v[3][3][3];
   int sweeps = 0, status = ORC_OK;
   double res = 0.0;
   long guards = 0;
   for (;;) {
-    guards = orc_patch_residual(n0, level, count, org, phi, delta, parent,
-                                parent_count, parent_org, alpha_B, kappa,
-                                branch, w, d);
-    if (guards < 0) { status = ORC_EINVAL; break; }
+    /* max |d| over the union (every 10 sweeps) */
+    int missing = 0;
     res = 0.0;
-    for (long c = 0; c < total; ++c) {
-      double a = fabs(d[c]);
-      if (!(a <= res)) res = a;
-    }
-    if (res != res) { status = ORC_ENAN; break; }
-    if (res < tol) break;
-    if (sweeps >= max_sweeps) { status = ORC_ENOCONV; break; }
+    guards = 0;
     for (int q = 0; q < count; ++q)
       for (int k = 0; k < ORC_PS; ++k)
         for (int j = 0; j < ORC_PS; ++j)
@@ -649,11 +661,28 @@ int orc_patch_solve(int n0, int level, int count, const int32_t* org,
             long c = (long)q * ORC_PC + orc_idx(i, j, k, ORC_PS);
             double L, dL;
             int g;
-            orc_gather_patch(&rl, phi, q, i, j, k, v);
+            missing |= orc_gather_patch(&rl, phi, q, i, j, k, v);
             orc_cell_operator(v, delta[c], h, &p, &L, &dL, &g);
-            phi[c] -= L / dL;
+            guards += g;
+            double a = fabs(L);
+            if (!(a <= res)) res = a;
           }
-    ++sweeps;
+    if (missing) { status = ORC_EINVAL; break; }
+    if (res != res) { status = ORC_ENAN; break; }
+    if (res < tol) break;
+    if (sweeps >= max_sweeps) { status = ORC_ENOCONV; break; }
+    for (int s = 0; s < 10; ++s, ++sweeps)
+      for (int q = 0; q < count; ++q)
+        for (int k = 0; k < ORC_PS; ++k)
+          for (int j = 0; j < ORC_PS; ++j)
+            for (int i = 0; i < ORC_PS; ++i) {
+              long c = (long)q * ORC_PC + orc_idx(i, j, k, ORC_PS);
+              double L, dL;
+              int g;
+              orc_gather_patch(&rl, phi, q, i, j, k, v);
+              orc_cell_operator(v, delta[c], h, &p, &L, &dL, &g);
+              phi[c] -= L / dL;
+            }
   }
   if (stats) {
     stats[0] = sweeps;
@@ -661,7 +690,6 @@ int orc_patch_solve(int n0, int level, int count, const int32_t* org,
     stats[2] = (double)guards;
     stats[3] = status;
   }
-  free(d);
   orc_reflevel_free(&rl);
   return status;
 }

@@ -37,6 +37,9 @@ def lib():
         L.orc_residual.restype = ctypes.c_long
         L.orc_residual.argtypes = [ctypes.c_int, ctypes.c_double, _D, _D, _D, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_int, ctypes.c_double, _D]
+        L.orc_density_floor.restype = ctypes.c_long
+        L.orc_density_floor.argtypes = [ctypes.c_long, _D, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, _D]
         L.orc_restrict.restype = None
         L.orc_restrict.argtypes = [ctypes.c_int, _D, _D]
         L.orc_prolong_add.restype = None
@@ -89,6 +92,14 @@ def residual(phi, delta, alpha, kappa, branch=0, f=None, w=W_PAPER):
     d = np.empty_like(phi)
     g = lib().orc_residual(n, 1.0 / n, _p(phi), _p(delta), _p(f), alpha, kappa, branch, w, _p(d))
     return d, int(g)
+
+
+def density_floor(delta, alpha, kappa, w=W_PAPER):
+    """delta held at 1 + 4(1-w) alpha kappa delta >= 0; returns (delta', cells changed)."""
+    delta = _f64(delta)
+    out = np.empty_like(delta)
+    hits = lib().orc_density_floor(delta.size, _p(delta), alpha, kappa, w, _p(out))
+    return out, int(hits)
 
 
 def restrict(fine):

@@ -1,0 +1,441 @@
+// C-ABI of libmg and the host orchestration of the FAS V-cycle
+// (Sec. III.C of arXiv:1303.0008).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_internal.h"
+#include "mg_solver.h"
+
+namespace mg {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace mg
+
+using namespace mg;
+
+#define MG_CK(call)                                                                   \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+      return MG_ECUDA;                                                                \
+    }                                                                                 \
+  } while (0)
+
+#define MG_FAIL(code, msg)  \
+  do {                      \
+    set_error(msg);         \
+    return code;            \
+  } while (0)
+
+extern "C" {
+
+const char* mg_last_error(void) { return g_last_error.c_str(); }
+
+void mg_default_options(mg_options* opt) {
+  if (!opt) return;
+  opt->prec = MG_FP64;
+  opt->nu_pre = 2;
+  opt->nu_post = 2;
+  opt->coarsest = 4;
+  opt->max_cycles = 100;
+  opt->inner_cycles = 3;
+  opt->use_graphs = 1;
+  opt->coarse_sweeps = 200;
+  opt->coarse_drop = 1e-6;
+  opt->time_kernels = 0;
+  opt->guard = MG_GUARD_FLOOR;
+  opt->patch_coarse_sweeps = 8;
+}
+
+static mg_status check_options(const mg_options& o) {
+  if (o.prec != MG_FP64 && o.prec != MG_MIXED) MG_FAIL(MG_EINVAL, "options: unknown precision");
+  if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post < 1 || o.nu_pre > 16 ||
+      o.nu_post > 16)
+    MG_FAIL(MG_EINVAL, "options: nu_pre/nu_post must be in [0,16] with a positive sum");
+  if (o.coarsest < 4) MG_FAIL(MG_EINVAL, "options: coarsest must be >= 4");
+  if (o.max_cycles < 0 || o.max_cycles > 100000) MG_FAIL(MG_EINVAL, "options: max_cycles");
+  if (o.inner_cycles < 1 || o.inner_cycles > 64) MG_FAIL(MG_EINVAL, "options: inner_cycles");
+  if (o.coarse_sweeps < 1 || o.coarse_sweeps > 100000) MG_FAIL(MG_EINVAL, "options: coarse_sweeps");
+  if (!(o.coarse_drop > 0.0 && o.coarse_drop < 1.0)) MG_FAIL(MG_EINVAL, "options: coarse_drop");
+  if (o.guard != MG_GUARD_FLOOR && o.guard != MG_GUARD_ROOT) MG_FAIL(MG_EINVAL, "options: guard");
+  if (o.patch_coarse_sweeps < 1 || o.patch_coarse_sweeps > 10000)
+    MG_FAIL(MG_EINVAL, "options: patch_coarse_sweeps");
+  return MG_OK;
+}
+
+mg_status mg_create_grid(mg_grid** out, int n, const mg_options* opt) {
+  if (!out) MG_FAIL(MG_EINVAL, "mg_create_grid: out is NULL");
+  *out = nullptr;
+  mg_options o;
+  mg_default_options(&o);
+  if (opt) o = *opt;
+  mg_status st = check_options(o);
+  if (st != MG_OK) return st;
+  Domain* d = nullptr;
+  st = domain_create(&d, n, o);
+  if (st != MG_OK) return st;
+  mg_grid* g = new (std::nothrow) mg_grid();
+  if (!g) {
+    domain_destroy(d);
+    MG_FAIL(MG_ENOMEM, "mg_create_grid: host allocation");
+  }
+  g->opt = o;
+  g->domains.push_back(d);
+  g->batch = false;
+  cudaGetDevice(&g->device);
+  if (cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    domain_destroy(d);
+    delete g;
+    MG_FAIL(MG_ECUDA, "mg_create_grid: stream creation failed");
+  }
+  g->stream = g->own_stream;
+  *out = g;
+  return MG_OK;
+}
+
+mg_status mg_create_batch(mg_grid** out, int count, const int* n, const mg_options* opt) {
+  if (!out || !n || count < 1 || count > 4096) MG_FAIL(MG_EINVAL, "mg_create_batch: bad arguments");
+  *out = nullptr;
+  mg_options o;
+  mg_default_options(&o);
+  if (opt) o = *opt;
+  mg_status st = check_options(o);
+  if (st != MG_OK) return st;
+  mg_grid* g = new (std::nothrow) mg_grid();
+  if (!g) MG_FAIL(MG_ENOMEM, "mg_create_batch: host allocation");
+  g->opt = o;
+  g->batch = true;
+  cudaGetDevice(&g->device);
+  for (int s = 0; s < count; ++s) {
+    Domain* d = nullptr;
+    st = domain_create(&d, n[s], o);
+    if (st != MG_OK) {
+      mg_destroy_grid(g);
+      return st;
+    }
+    g->domains.push_back(d);
+  }
+  if (cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    mg_destroy_grid(g);
+    MG_FAIL(MG_ECUDA, "mg_create_batch: stream creation failed");
+  }
+  g->stream = g->own_stream;
+  st = batch_prepare(g);
+  if (st != MG_OK) {
+    mg_destroy_grid(g);
+    return st;
+  }
+  *out = g;
+  return MG_OK;
+}
+
+void mg_destroy_grid(mg_grid* g) {
+  if (!g) return;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  for (Domain* d : g->domains) domain_destroy(d);
+  for (auto& pl : g->patch_levels) patch_level_destroy(pl);
+  batch_release(g);
+  if (g->force_tmp) cudaFree(g->force_tmp);
+  if (g->own_stream) cudaStreamDestroy(g->own_stream);
+  delete g;
+}
+
+mg_status mg_set_stream(mg_grid* g, void* stream) {
+  if (!g) MG_FAIL(MG_EINVAL, "mg_set_stream: NULL handle");
+  MG_CK(cudaStreamSynchronize(g->stream));
+  g->stream = stream ? (cudaStream_t)stream : g->own_stream;
+  for (Domain* d : g->domains) domain_invalidate_graphs(d);
+  return MG_OK;
+}
+
+static mg_status copy_in(mg_grid* g, double* dst, const double* src, size_t count, int on_device) {
+  if (!src) MG_FAIL(MG_EINVAL, "input pointer is NULL");
+  MG_CK(cudaMemcpyAsync(dst, src, count * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        g->stream));
+  if (!on_device) MG_CK(cudaStreamSynchronize(g->stream));
+  return MG_OK;
+}
+
+static mg_status copy_out(const mg_grid* g, double* dst, const double* src, size_t count,
+                          int on_device) {
+  if (!dst) MG_FAIL(MG_EINVAL, "output pointer is NULL");
+  MG_CK(cudaMemcpyAsync(dst, src, count * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        g->stream));
+  if (!on_device) MG_CK(cudaStreamSynchronize(g->stream));
+  return MG_OK;
+}
+
+// Resolve (level, patch) to a device range.
+static mg_status resolve(const mg_grid* g, int level, int patch, bool field, double** ptr,
+                         size_t* count) {
+  if (g->batch) {
+    if (level != 0 || patch < 0 || patch >= (int)g->domains.size())
+      MG_FAIL(MG_EINVAL, "batch handle: level must be 0 and patch a solve index");
+    Domain* d = g->domains[patch];
+    *ptr = field ? d->lv[0].phi : d->lv[0].delta;
+    *count = (size_t)d->lv[0].cells;
+    return MG_OK;
+  }
+  if (level == 0) {
+    if (patch != -1) MG_FAIL(MG_EINVAL, "level 0 takes patch = -1");
+    Domain* d = g->domains[0];
+    *ptr = field ? d->lv[0].phi : d->lv[0].delta;
+    *count = (size_t)d->lv[0].cells;
+    return MG_OK;
+  }
+  if (level < 1 || level > (int)g->patch_levels.size() || !g->patch_levels[level - 1])
+    MG_FAIL(MG_EINVAL, "no patches on that level");
+  PatchLevel* pl = g->patch_levels[level - 1];
+  if (patch < -1 || patch >= pl->count) MG_FAIL(MG_EINVAL, "patch index out of range");
+  double* base = field ? pl->phi : pl->delta;
+  if (patch == -1) {
+    *ptr = base;
+    *count = (size_t)pl->count * 512;
+  } else {
+    *ptr = base + (size_t)patch * 512;
+    *count = 512;
+  }
+  return MG_OK;
+}
+
+mg_status mg_set_density(mg_grid* g, int level, int patch, const double* delta, int on_device) {
+  if (!g) MG_FAIL(MG_EINVAL, "mg_set_density: NULL handle");
+  double* dst;
+  size_t cnt;
+  mg_status st = resolve(g, level, patch, false, &dst, &cnt);
+  if (st != MG_OK) return st;
+  st = copy_in(g, dst, delta, cnt, on_device);
+  if (st != MG_OK) return st;
+  if (level == 0) {
+    Domain* d = g->batch ? g->domains[patch] : g->domains[0];
+    domain_restrict_density(d, g->stream);
+    d->density_set = true;
+    MG_CK(cudaGetLastError());
+  } else {
+    patch_restrict_density(g, g->patch_levels[level - 1]);
+    MG_CK(cudaGetLastError());
+    g->patch_levels[level - 1]->density_set = true;
+  }
+  return MG_OK;
+}
+
+mg_status mg_set_field(mg_grid* g, int level, int patch, const double* phi, int on_device) {
+  if (!g) MG_FAIL(MG_EINVAL, "mg_set_field: NULL handle");
+  double* dst;
+  size_t cnt;
+  mg_status st = resolve(g, level, patch, true, &dst, &cnt);
+  if (st != MG_OK) return st;
+  return copy_in(g, dst, phi, cnt, on_device);
+}
+
+mg_status mg_get_field(const mg_grid* g, int level, int patch, double* out, int on_device) {
+  if (!g) MG_FAIL(MG_EINVAL, "mg_get_field: NULL handle");
+  double* src;
+  size_t cnt;
+  mg_status st = resolve(g, level, patch, true, &src, &cnt);
+  if (st != MG_OK) return st;
+  return copy_out(g, out, src, cnt, on_device);
+}
+
+mg_status mg_get_force(const mg_grid* g_const, int level, int patch, double* out, int on_device) {
+  mg_grid* g = const_cast<mg_grid*>(g_const);
+  if (!g) MG_FAIL(MG_EINVAL, "mg_get_force: NULL handle");
+  if (!out) MG_FAIL(MG_EINVAL, "mg_get_force: out is NULL");
+  double* src;
+  size_t cnt;
+  mg_status st = resolve(g, level, patch, true, &src, &cnt);
+  if (st != MG_OK) return st;
+  const size_t bytes = 3 * cnt * sizeof(double);
+  double* dst = out;
+  if (!on_device) {
+    if (g->force_tmp_bytes < bytes) {
+      if (g->force_tmp) cudaFree(g->force_tmp);
+      g->force_tmp = nullptr;
+      g->force_tmp_bytes = 0;
+      if (cudaMalloc(&g->force_tmp, bytes) != cudaSuccess)
+        MG_FAIL(MG_ENOMEM, "mg_get_force: device allocation");
+      g->force_tmp_bytes = bytes;
+    }
+    dst = g->force_tmp;
+  }
+  if (g->batch || level == 0) {
+    Domain* d = g->batch ? g->domains[patch] : g->domains[0];
+    launch_force64(g->stream, d->n, d->lv[0].phi, dst);
+  } else {
+    st = patch_force(g, level, patch, dst);
+    if (st != MG_OK) return st;
+  }
+  MG_CK(cudaGetLastError());
+  if (!on_device) {
+    MG_CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, g->stream));
+    MG_CK(cudaStreamSynchronize(g->stream));
+  }
+  return MG_OK;
+}
+
+mg_status mg_add_patches(mg_grid* g, int level, int count, const int32_t* origin) {
+  if (!g || g->batch) MG_FAIL(MG_EINVAL, "mg_add_patches: needs a domain handle");
+  return patches_add(g, level, count, origin);
+}
+
+static mg_status check_branch(int branch, double alpha) {
+  if (branch < -1 || branch > 1) MG_FAIL(MG_EINVAL, "branch must be -1, 0 or +1");
+  if (alpha == 0.0 && branch != 0) MG_FAIL(MG_EINVAL, "alpha = 0 is linear: branch must be 0");
+  if (!std::isfinite(alpha)) MG_FAIL(MG_EINVAL, "alpha must be finite");
+  return MG_OK;
+}
+
+mg_status mg_solve(mg_grid* g, int branch, double alpha, double kappa, double tol,
+                   mg_solve_stats* stats) {
+  if (!g || g->batch) MG_FAIL(MG_EINVAL, "mg_solve: needs a domain handle");
+  mg_status st = check_branch(branch, alpha);
+  if (st != MG_OK) return st;
+  if (!std::isfinite(kappa) || !(tol > 0.0)) MG_FAIL(MG_EINVAL, "mg_solve: kappa/tol");
+  Domain* d = g->domains[0];
+  if (!d->density_set) MG_FAIL(MG_ESTATE, "mg_solve: density not set");
+  mg_solve_stats local;
+  mg_solve_stats* s = stats ? stats : &local;
+  st = domain_solve(d, g->opt, g->stream, branch, alpha, kappa, tol, s);
+  if (st != MG_OK) return st;
+  for (size_t l = 0; l < g->patch_levels.size(); ++l) {
+    PatchLevel* pl = g->patch_levels[l];
+    if (!pl || pl->count == 0) continue;
+    if (!pl->density_set) MG_FAIL(MG_ESTATE, "mg_solve: patch density not set");
+    mg_status ps = patch_level_solve(g, (int)l + 1, branch, alpha, kappa, tol);
+    if (ps != MG_OK) return ps;
+  }
+  return MG_OK;
+}
+
+mg_status mg_solve_batch(mg_grid* g, const int* branch, const double* alpha, const double* kappa,
+                         double tol, mg_solve_stats* stats) {
+  if (!g || !g->batch) MG_FAIL(MG_EINVAL, "mg_solve_batch: needs a batch handle");
+  if (!branch || !alpha || !kappa || !(tol > 0.0)) MG_FAIL(MG_EINVAL, "mg_solve_batch: arguments");
+  for (size_t s = 0; s < g->domains.size(); ++s) {
+    mg_status st = check_branch(branch[s], alpha[s]);
+    if (st != MG_OK) return st;
+    if (!std::isfinite(kappa[s])) MG_FAIL(MG_EINVAL, "mg_solve_batch: kappa");
+    if (!g->domains[s]->density_set) MG_FAIL(MG_ESTATE, "mg_solve_batch: density not set");
+  }
+  return batch_solve(g, branch, alpha, kappa, tol, stats);
+}
+
+// ---------------------------------------------------------------------------
+// Single-kernel entry points
+// ---------------------------------------------------------------------------
+static mg_status check_n(int n) {
+  if (n < 4 || (n & 1) || n > 2048) MG_FAIL(MG_EINVAL, "n must be even and in [4, 2048]");
+  return MG_OK;
+}
+
+struct TmpBuf {
+  void* p = nullptr;
+  ~TmpBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+mg_status mg_op_residual(int n, const double* phi, const double* delta, const double* f,
+                         int branch, double alpha, double kappa, double* d, double* norms,
+                         void* stream) {
+  mg_status st = check_n(n);
+  if (st != MG_OK) return st;
+  st = check_branch(branch, alpha);
+  if (st != MG_OK) return st;
+  if (!phi || !delta) MG_FAIL(MG_EINVAL, "mg_op_residual: NULL input");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long cells = (long long)n * n * n;
+  const OpConst64 c = make_op64(n, alpha, kappa, branch);
+  TmpBuf src, part, sc;
+  if (cudaMalloc(&src.p, cells * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&part.p, partials_needed(cells) * sizeof(Partial)) != cudaSuccess ||
+      cudaMalloc(&sc.p, sizeof(LevelScalars)) != cudaSuccess)
+    MG_FAIL(MG_ENOMEM, "mg_op_residual: device allocation");
+  double a, b;
+  src_coefficients(c, kappa, &a, &b);
+  launch_affine64(s, cells, delta, (double*)src.p, a, b);
+  launch_residual64(s, n, phi, (double*)src.p, f, d, c, (Partial*)part.p, (LevelScalars*)sc.p, 1);
+  MG_CK(cudaGetLastError());
+  LevelScalars h;
+  MG_CK(cudaMemcpyAsync(&h, sc.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  MG_CK(cudaStreamSynchronize(s));
+  if (norms) {
+    norms[0] = h.sum;
+    norms[1] = h.dmax;
+    norms[2] = h.dmin;
+    norms[3] = (double)h.guards;
+    norms[4] = (double)h.nonfinite;
+  }
+  return MG_OK;
+}
+
+mg_status mg_op_smooth(int n, double* phi, const double* delta, const double* f, int branch,
+                       double alpha, double kappa, double lambda, int sweeps, void* stream) {
+  mg_status st = check_n(n);
+  if (st != MG_OK) return st;
+  st = check_branch(branch, alpha);
+  if (st != MG_OK) return st;
+  if (!phi || !delta || sweeps < 0) MG_FAIL(MG_EINVAL, "mg_op_smooth: arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long cells = (long long)n * n * n;
+  const OpConst64 c = make_op64(n, alpha, kappa, branch);
+  TmpBuf src, sc;
+  if (cudaMalloc(&src.p, cells * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&sc.p, sizeof(LevelScalars)) != cudaSuccess)
+    MG_FAIL(MG_ENOMEM, "mg_op_smooth: device allocation");
+  LevelScalars h{};
+  h.lambda = lambda;
+  MG_CK(cudaMemcpyAsync(sc.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  double a, b;
+  src_coefficients(c, kappa, &a, &b);
+  launch_affine64(s, cells, delta, (double*)src.p, a, b);
+  launch_smooth64(s, n, phi, (double*)src.p, f, (LevelScalars*)sc.p, c, sweeps);
+  MG_CK(cudaGetLastError());
+  MG_CK(cudaStreamSynchronize(s));
+  return MG_OK;
+}
+
+mg_status mg_op_restrict(int n, const double* fine, double* coarse, void* stream) {
+  mg_status st = check_n(n);
+  if (st != MG_OK) return st;
+  if (!fine || !coarse) MG_FAIL(MG_EINVAL, "mg_op_restrict: NULL pointer");
+  launch_restrict64((cudaStream_t)stream, n / 2, fine, coarse);
+  MG_CK(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_op_prolong_correct(int n, const double* coarse, const double* coarse_ref,
+                                double* fine, void* stream) {
+  mg_status st = check_n(n);
+  if (st != MG_OK) return st;
+  if (n / 2 < 2 || !coarse || !coarse_ref || !fine)
+    MG_FAIL(MG_EINVAL, "mg_op_prolong_correct: arguments");
+  launch_prolong_correct64((cudaStream_t)stream, n / 2, coarse, coarse_ref, fine);
+  MG_CK(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_op_force(int n, const double* phi, double* out, void* stream) {
+  mg_status st = check_n(n);
+  if (st != MG_OK) return st;
+  if (!phi || !out) MG_FAIL(MG_EINVAL, "mg_op_force: NULL pointer");
+  launch_force64((cudaStream_t)stream, n, phi, out);
+  MG_CK(cudaGetLastError());
+  return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// Device-side building blocks shared by the CUDA kernels of libmg.
+//
+// The discrete operator is the one of Sec. III.B of arXiv:1303.0008 (the L^h
+// equation with its Sigma_ijk), written for the operator-splitting constant
+// w = 1/3 (Sec. III.A).  With w = 1/3 the non-source part of Sigma,
+//     Sigma_d h^4 = [(Sx-Sy)^2 + (Sx-Sz)^2 + (Sy-Sz)^2]/3 + (Cxy^2 + Cxz^2 + Cyz^2)/8,
+// (Sx = phi_{i+1} + phi_{i-1}, Cxy the four-point cross difference), does not
+// involve the centre value, so the Newton step of Sec. III.B is the exact
+// pointwise solve of L^h phi = rhs for the centre cell.
+//
+// Parameters follow the library convention: alpha is the coefficient of the
+// nonlinear term of Eq. code_eqn (the paper's alpha is 1/alpha), kappa the source
+// coefficient.  With u = kappa*delta + alpha*Sigma_d and q = 1 + 4(1-w) alpha u,
+// the root of Eq. two_branch is D = (sigma sqrt(q) - 1) / (2(1-w) alpha) where
+// sigma = +1 picks the physical root of Eq. one_branch.  When q < 0 the square
+// root is taken of 0 (the real part of the complex root) and the cell counts as
+// guarded.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mg {
+
+// How the root D is evaluated.
+enum OpMode : int {
+  OP_LINEAR = 0,  // alpha == 0: D = kappa*delta
+  OP_SQRT = 1,    // D = k2 (sigma sqrt(q) - 1); src = 1 + c3 kappa delta
+  OP_CONJ = 2     // physical root as 2u/(1+sqrt(q)) for small |alpha|; src = kappa delta
+};
+
+// Per-level constants of the FP64 operator.
+struct OpConst64 {
+  double h2;      // h^2
+  double inv_h2;  // 1/h^2
+  double e1, e2;  // OP_SQRT: q = src + e1*A + e2*B
+  double c1, c2;  // OP_CONJ: u = src + c1*A + c2*B
+  double c3;      // 4(1-w) alpha
+  double k2s;     // sigma * k2, k2 = 2/c3
+  double k2;
+  int mode;
+};
+
+// Per-level constants of the FP32 correction operator (mixed precision).
+struct OpConst32 {
+  float h2, inv_h2;
+  float g1, g2;   // alpha/(3h^4), alpha/(8h^4): Delta u = g1*dA + g2*dB
+  float c3;       // 4(1-w) alpha
+  float k2;       // 2/c3 (0 when alpha == 0)
+  float sigma;    // +1 physical root, -1 the other one
+  int linear;     // alpha == 0
+};
+
+// Scalars that a residual evaluation leaves for one level.
+struct LevelScalars {
+  double lambda;     // compatibility constant mean(d) (periodic), 0 (Dirichlet)
+  double res;        // max |d - lambda|
+  double sum;        // sum of d
+  double dmax, dmin;
+  long long guards;  // cells with q < 0
+  long long nonfinite;
+  unsigned long long floored;  // cells whose source was held at the real-root bound
+};
+
+__device__ __forceinline__ int wrap_up(int i, int n) { return (i + 1 == n) ? 0 : i + 1; }
+__device__ __forceinline__ int wrap_dn(int i, int n) { return (i == 0) ? n - 1 : i - 1; }
+
+__device__ __forceinline__ long long lidx(int i, int j, int k, int n) {
+  return (long long)i + (long long)n * ((long long)j + (long long)n * (long long)k);
+}
+
+// The 18 stencil neighbours of one cell in the form the operator uses.
+struct Stencil64 {
+  double sx, sy, sz;     // face pair sums
+  double cxy, cxz, cyz;  // cross differences (without the 1/4)
+};
+
+template <typename T>
+struct StencilT {
+  T sx, sy, sz, cxy, cxz, cyz;
+};
+
+// Gather the face sums and cross differences of cell (i,j,k) of a periodic n^3
+// array.
+template <typename T>
+__device__ __forceinline__ StencilT<T> gather_periodic(const T* __restrict__ p, int i, int j,
+                                                       int k, int n) {
+  const int ip = wrap_up(i, n), im = wrap_dn(i, n);
+  const int jp = wrap_up(j, n), jm = wrap_dn(j, n);
+  const int kp = wrap_up(k, n), km = wrap_dn(k, n);
+  StencilT<T> s;
+  s.sx = p[lidx(ip, j, k, n)] + p[lidx(im, j, k, n)];
+  s.sy = p[lidx(i, jp, k, n)] + p[lidx(i, jm, k, n)];
+  s.sz = p[lidx(i, j, kp, n)] + p[lidx(i, j, km, n)];
+  s.cxy = (p[lidx(ip, jp, k, n)] + p[lidx(im, jm, k, n)]) -
+          (p[lidx(ip, jm, k, n)] + p[lidx(im, jp, k, n)]);
+  s.cxz = (p[lidx(ip, j, kp, n)] + p[lidx(im, j, km, n)]) -
+          (p[lidx(ip, j, km, n)] + p[lidx(im, j, kp, n)]);
+  s.cyz = (p[lidx(i, jp, kp, n)] + p[lidx(i, jm, km, n)]) -
+          (p[lidx(i, jp, km, n)] + p[lidx(i, jm, kp, n)]);
+  return s;
+}
+
+// D (the root of Eq. two_branch) from the stencil and the per-cell source term.
+// `guard` is set when the discriminant is negative.
+__device__ __forceinline__ double root_D(const StencilT<double>& s, double src,
+                                         const OpConst64& c, bool& guard) {
+  if (c.mode == OP_LINEAR) {
+    guard = false;
+    return src;
+  }
+  const double a1 = s.sx - s.sy, a2 = s.sx - s.sz, a3 = s.sy - s.sz;
+  const double A = fma(a1, a1, fma(a2, a2, a3 * a3));
+  const double B = fma(s.cxy, s.cxy, fma(s.cxz, s.cxz, s.cyz * s.cyz));
+  if (c.mode == OP_SQRT) {
+    const double q = fma(c.e1, A, fma(c.e2, B, src));
+    guard = q < 0.0;
+    const double r = sqrt(guard ? 0.0 : q);  // a NaN q stays NaN
+    return fma(c.k2s, r, -c.k2);
+  }
+  const double u = fma(c.c1, A, fma(c.c2, B, src));
+  const double q = fma(c.c3, u, 1.0);
+  guard = q < 0.0;
+  if (guard) return -c.k2;
+  return (2.0 * u) / (1.0 + sqrt(q));
+}
+
+// Deterministic block reduction of (sum, max, min, guards, nonfinite).
+struct Partial {
+  double sum, dmax, dmin;
+  long long guards, nonfinite;
+};
+
+__device__ __forceinline__ void partial_init(Partial& p) {
+  p.sum = 0.0;
+  p.dmax = -INFINITY;
+  p.dmin = INFINITY;
+  p.guards = 0;
+  p.nonfinite = 0;
+}
+
+__device__ __forceinline__ void partial_add(Partial& p, double d, bool guard) {
+  if (isfinite(d)) {
+    p.sum += d;
+    p.dmax = fmax(p.dmax, d);
+    p.dmin = fmin(p.dmin, d);
+  } else {
+    p.nonfinite += 1;
+  }
+  p.guards += guard ? 1 : 0;
+}
+
+__device__ __forceinline__ void partial_merge(Partial& a, const Partial& b) {
+  a.sum += b.sum;
+  a.dmax = fmax(a.dmax, b.dmax);
+  a.dmin = fmin(a.dmin, b.dmin);
+  a.guards += b.guards;
+  a.nonfinite += b.nonfinite;
+}
+
+__device__ __forceinline__ Partial warp_reduce(Partial p) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Partial q;
+    q.sum = __shfl_down_sync(0xffffffffu, p.sum, o);
+    q.dmax = __shfl_down_sync(0xffffffffu, p.dmax, o);
+    q.dmin = __shfl_down_sync(0xffffffffu, p.dmin, o);
+    q.guards = __shfl_down_sync(0xffffffffu, p.guards, o);
+    q.nonfinite = __shfl_down_sync(0xffffffffu, p.nonfinite, o);
+    partial_merge(p, q);
+  }
+  return p;
+}
+
+// Reduce over the block; thread 0 returns the block's value.  blockDim.x must
+// be a multiple of 32 and at most 1024.
+__device__ __forceinline__ Partial block_reduce(Partial p) {
+  __shared__ Partial sh[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  p = warp_reduce(p);
+  if (lane == 0) sh[wid] = p;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (wid == 0) {
+    Partial q;
+    if (lane < nw) q = sh[lane];
+    else partial_init(q);
+    q = warp_reduce(q);
+    p = q;
+  }
+  __syncthreads();
+  return p;
+}
+
+}  // namespace mg

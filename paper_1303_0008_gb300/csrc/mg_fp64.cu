@@ -1,0 +1,474 @@
+// FP64 kernels of the periodic FAS V-cycle (Sec. III.B and III.C of
+// arXiv:1303.0008): four-colour Newton-Gauss-Seidel sweep, residual with its
+// norms, residual evaluation fused with full-weighting restriction, the coarse
+// FAS right-hand side, trilinear prolongation of the correction, the coarsest
+// solve in one CTA, density restriction, gauge fix and the force output.
+//
+// Every kernel works on dense n^3 arrays, x fastest (idx = i + n(j + n k)), with
+// periodic wrap.  They are FP64-ALU bound on GB300 (about 35-45 FP64 operations
+// per cell against 24 bytes of traffic), so they favour a low FP64 instruction
+// count over memory tiling.
+#include "mg_common.cuh"
+#include "mg_internal.h"
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// Four-colour Gauss-Seidel: colour c = ((i+k)&1) + 2((j+k)&1).  No face or edge
+// neighbour of a cell shares its colour (only the corners do, and they are not
+// in the 19-point stencil), so the cells of one colour update independently
+// and each update is the exact Newton step of Sec. III.B.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_smooth_colour64(int n, double* __restrict__ phi,
+                                                         const double* __restrict__ src,
+                                                         const double* __restrict__ f,
+                                                         const LevelScalars* __restrict__ sc,
+                                                         OpConst64 c, int colour) {
+  const int hn = n >> 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)hn * hn * n;
+  if (t >= total) return;
+  const int m = (int)(t % hn);
+  const long long rest = t / hn;
+  const int jj = (int)(rest % hn);
+  const int k = (int)(rest / hn);
+  const int i = 2 * m + ((colour ^ k) & 1);
+  const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
+  const long long id = lidx(i, j, k, n);
+  const StencilT<double> s = gather_periodic(phi, i, j, k, n);
+  bool g;
+  const double D = root_D(s, src[id], c, g);
+  double rhs = sc->lambda;
+  if (f) rhs += f[id];
+  const double lapnb = s.sx + s.sy + s.sz;
+  phi[id] = fma(-c.h2, D + rhs, lapnb) * (1.0 / 6.0);
+}
+
+// d = L^h phi - f with block partial norms.
+__global__ void __launch_bounds__(256) k_residual64(int n, const double* __restrict__ phi,
+                                                    const double* __restrict__ src,
+                                                    const double* __restrict__ f,
+                                                    double* __restrict__ dout, OpConst64 c,
+                                                    Partial* __restrict__ partials) {
+  const long long cells = (long long)n * n * n;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  Partial p;
+  partial_init(p);
+  if (t < cells) {
+    const int i = (int)(t % n);
+    const int j = (int)((t / n) % n);
+    const int k = (int)(t / ((long long)n * n));
+    const StencilT<double> s = gather_periodic(phi, i, j, k, n);
+    bool g;
+    const double D = root_D(s, src[t], c, g);
+    const double lap = (s.sx + s.sy + s.sz) - 6.0 * phi[t];
+    double d = fma(lap, c.inv_h2, -D);
+    if (f) d -= f[t];
+    if (dout) dout[t] = d;
+    partial_add(p, d, g);
+  }
+  p = block_reduce(p);
+  if (threadIdx.x == 0) partials[blockIdx.x] = p;
+}
+
+// Residual of the 8 children of each coarse cell, averaged (full weighting),
+// together with R phi; the partial norms cover every fine cell.
+__global__ void __launch_bounds__(128) k_residual_restrict64(
+    int nf, const double* __restrict__ phi, const double* __restrict__ src,
+    const double* __restrict__ f, OpConst64 c, double* __restrict__ phi_c,
+    double* __restrict__ phihat_c, double* __restrict__ rd_c, Partial* __restrict__ partials) {
+  const int nc = nf >> 1;
+  const long long ccells = (long long)nc * nc * nc;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  Partial p;
+  partial_init(p);
+  if (t < ccells) {
+    const int I = (int)(t % nc);
+    const int J = (int)((t / nc) % nc);
+    const int K = (int)(t / ((long long)nc * nc));
+    double sphi = 0.0, sd = 0.0;
+#pragma unroll 1
+    for (int ch = 0; ch < 8; ++ch) {
+      const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
+      const long long id = lidx(i, j, k, nf);
+      const StencilT<double> s = gather_periodic(phi, i, j, k, nf);
+      bool g;
+      const double D = root_D(s, src[id], c, g);
+      const double ctr = phi[id];
+      const double lap = (s.sx + s.sy + s.sz) - 6.0 * ctr;
+      double d = fma(lap, c.inv_h2, -D);
+      if (f) d -= f[id];
+      partial_add(p, d, g);
+      sphi += ctr;
+      sd += d;
+    }
+    phi_c[t] = sphi * 0.125;
+    phihat_c[t] = sphi * 0.125;
+    rd_c[t] = sd * 0.125;
+  }
+  p = block_reduce(p);
+  if (threadIdx.x == 0) partials[blockIdx.x] = p;
+}
+
+// One block: reduce the partials in a fixed order and publish the scalars.
+__global__ void __launch_bounds__(256) k_finalize(const Partial* __restrict__ partials, int nparts,
+                                                  double cells, int periodic,
+                                                  LevelScalars* __restrict__ sc) {
+  Partial p;
+  partial_init(p);
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) partial_merge(p, partials[b]);
+  p = block_reduce(p);
+  if (threadIdx.x == 0) {
+    const double lam = periodic ? p.sum / cells : 0.0;
+    sc->lambda = lam;
+    sc->sum = p.sum;
+    sc->dmax = p.dmax;
+    sc->dmin = p.dmin;
+    sc->res = (p.nonfinite > 0) ? NAN : fmax(p.dmax - lam, lam - p.dmin);
+    sc->guards = p.guards;
+    sc->nonfinite = p.nonfinite;
+  }
+}
+
+// f^H = L^H(R phi) - (R d - lambda^h); lambda^H starts at 0.
+__global__ void __launch_bounds__(256) k_fas_rhs64(int nc, const double* __restrict__ phi_c,
+                                                   const double* __restrict__ src_c,
+                                                   double* __restrict__ f_c, OpConst64 c,
+                                                   const LevelScalars* __restrict__ fine_sc,
+                                                   LevelScalars* __restrict__ coarse_sc) {
+  const long long cells = (long long)nc * nc * nc;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) coarse_sc->lambda = 0.0;
+  if (t >= cells) return;
+  const int i = (int)(t % nc);
+  const int j = (int)((t / nc) % nc);
+  const int k = (int)(t / ((long long)nc * nc));
+  const StencilT<double> s = gather_periodic(phi_c, i, j, k, nc);
+  bool g;
+  const double D = root_D(s, src_c[t], c, g);
+  const double lap = (s.sx + s.sy + s.sz) - 6.0 * phi_c[t];
+  const double L = fma(lap, c.inv_h2, -D);
+  f_c[t] = L - f_c[t] + fine_sc->lambda;
+}
+
+// phi^h += P(phi^H - R phi^h): cell-centred trilinear, per axis 3/4 on the parent
+// and 1/4 on the parent's neighbour on the child's side.
+__global__ void __launch_bounds__(256) k_prolong_correct64(int nc, const double* __restrict__ phi_c,
+                                                           const double* __restrict__ phihat_c,
+                                                           double* __restrict__ phi_f) {
+  const int nf = nc << 1;
+  const long long cells = (long long)nf * nf * nf;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  const int i = (int)(t % nf);
+  const int j = (int)((t / nf) % nf);
+  const int k = (int)(t / ((long long)nf * nf));
+  const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+  const int I1 = (i & 1) ? wrap_up(I0, nc) : wrap_dn(I0, nc);
+  const int J1 = (j & 1) ? wrap_up(J0, nc) : wrap_dn(J0, nc);
+  const int K1 = (k & 1) ? wrap_up(K0, nc) : wrap_dn(K0, nc);
+  auto e = [&](int a, int b, int cc) {
+    const long long q = lidx(a, b, cc, nc);
+    return phi_c[q] - phihat_c[q];
+  };
+  const double v = 27.0 * e(I0, J0, K0) + 9.0 * (e(I1, J0, K0) + e(I0, J1, K0) + e(I0, J0, K1)) +
+                   3.0 * (e(I1, J1, K0) + e(I1, J0, K1) + e(I0, J1, K1)) + e(I1, J1, K1);
+  phi_f[t] += v * (1.0 / 64.0);
+}
+
+// Coarsest level in one CTA (n^3 <= 4096 cells in shared memory): four-colour
+// sweeps until max|d - lambda| has fallen by `drop` or `max_sweeps` sweeps.
+__global__ void __launch_bounds__(256) k_coarsest64(int n, double* __restrict__ phi,
+                                                    const double* __restrict__ src,
+                                                    const double* __restrict__ f, OpConst64 c,
+                                                    LevelScalars* __restrict__ sc, int max_sweeps,
+                                                    double drop, int check_every) {
+  extern __shared__ double smem64[];
+  __shared__ double s_lam, s_res0, s_res;
+  const int cells = n * n * n;
+  double* sphi = smem64;
+  double* ssrc = smem64 + cells;
+  double* sf = smem64 + 2 * cells;
+  for (int q = threadIdx.x; q < cells; q += blockDim.x) {
+    sphi[q] = phi[q];
+    ssrc[q] = src[q];
+    sf[q] = f ? f[q] : 0.0;
+  }
+  if (threadIdx.x == 0) s_lam = sc->lambda;
+  __syncthreads();
+  auto residual = [&](double& res_out) {
+    Partial p;
+    partial_init(p);
+    for (int q = threadIdx.x; q < cells; q += blockDim.x) {
+      const int i = q % n, j = (q / n) % n, k = q / (n * n);
+      const StencilT<double> s = gather_periodic<double>(sphi, i, j, k, n);
+      bool g;
+      const double D = root_D(s, ssrc[q], c, g);
+      const double lap = (s.sx + s.sy + s.sz) - 6.0 * sphi[q];
+      partial_add(p, fma(lap, c.inv_h2, -D) - sf[q], g);
+    }
+    p = block_reduce(p);
+    if (threadIdx.x == 0) {
+      const double lam = p.sum / (double)cells;
+      s_lam = lam;
+      s_res = (p.nonfinite > 0) ? NAN : fmax(p.dmax - lam, lam - p.dmin);
+      sc->guards = p.guards;
+      sc->nonfinite = p.nonfinite;
+    }
+    __syncthreads();
+    res_out = s_res;
+  };
+  double r;
+  residual(r);
+  if (threadIdx.x == 0) s_res0 = r;
+  __syncthreads();
+  const double r0 = s_res0;
+  const int hn = n >> 1;
+  const int per_colour = hn * hn * n;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int colour = 0; colour < 4; ++colour) {
+      for (int t = threadIdx.x; t < per_colour; t += blockDim.x) {
+        const int m = t % hn, jj = (t / hn) % hn, k = t / (hn * hn);
+        const int i = 2 * m + ((colour ^ k) & 1);
+        const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
+        const int id = i + n * (j + n * k);
+        const StencilT<double> s = gather_periodic<double>(sphi, i, j, k, n);
+        bool g;
+        const double D = root_D(s, ssrc[id], c, g);
+        sphi[id] = fma(-c.h2, D + sf[id] + s_lam, s.sx + s.sy + s.sz) * (1.0 / 6.0);
+      }
+      __syncthreads();
+    }
+    if ((sweep + 1) % check_every == 0 || sweep + 1 == max_sweeps) {
+      residual(r);
+      if (!(r > drop * r0)) break;
+    }
+  }
+  for (int q = threadIdx.x; q < cells; q += blockDim.x) phi[q] = sphi[q];
+  if (threadIdx.x == 0) {
+    sc->lambda = s_lam;
+    sc->res = s_res;
+  }
+}
+
+// coarse = mean of the 8 children.
+__global__ void __launch_bounds__(256) k_restrict64(int nc, const double* __restrict__ fine,
+                                                    double* __restrict__ coarse) {
+  const int nf = nc << 1;
+  const long long cells = (long long)nc * nc * nc;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  const int I = (int)(t % nc);
+  const int J = (int)((t / nc) % nc);
+  const int K = (int)(t / ((long long)nc * nc));
+  double s = 0.0;
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch)
+    s += fine[lidx(2 * I + (ch & 1), 2 * J + ((ch >> 1) & 1), 2 * K + (ch >> 2), nf)];
+  coarse[t] = s * 0.125;
+}
+
+// src = a * delta + b, optionally held where 1 + c3 kappa delta < 0 (the bound under
+// which the root of Eq. two_branch stays real for any field): in the sqrt form
+// (b = 1) src >= 0, in the kappa*delta form c3 * src >= -1.  Floored cells are
+// counted into *floored.
+__global__ void __launch_bounds__(256) k_affine64(long long cells, const double* __restrict__ delta,
+                                                  double* __restrict__ out, double a, double b,
+                                                  double c3, int floor,
+                                                  unsigned long long* __restrict__ floored) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  bool hit = false;
+  if (t < cells) {
+    double v = fma(a, delta[t], b);
+    if (floor) {
+      const double lhs = (b != 0.0) ? v : fma(c3, v, 1.0);  // 1 + c3 kappa delta
+      if (lhs < 0.0) {
+        hit = true;
+        v = (b != 0.0) ? 0.0 : -1.0 / c3;
+      }
+    }
+    out[t] = v;
+  }
+  if (floored) {
+    const unsigned ballot = __ballot_sync(0xffffffffu, hit);
+    if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(floored, (unsigned long long)__popc(ballot));
+  }
+}
+
+// Partial sums of x (for the gauge fix).
+__global__ void __launch_bounds__(256) k_sum_partials(long long cells, const double* __restrict__ x,
+                                                      Partial* __restrict__ partials) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  Partial p;
+  partial_init(p);
+  if (t < cells) partial_add(p, x[t], false);
+  p = block_reduce(p);
+  if (threadIdx.x == 0) partials[blockIdx.x] = p;
+}
+
+// x -= mean (the mean sits in sc->lambda, computed by k_finalize).
+__global__ void __launch_bounds__(256) k_sub_mean(long long cells, double* __restrict__ x,
+                                                  const LevelScalars* __restrict__ sc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < cells) x[t] -= sc->lambda;
+}
+
+// g = -(1/2) grad phi, central differences; out is 3 x n^3 (x, y, z).
+__global__ void __launch_bounds__(256) k_force64(int n, const double* __restrict__ phi,
+                                                 double* __restrict__ out) {
+  const long long cells = (long long)n * n * n;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  const int i = (int)(t % n);
+  const int j = (int)((t / n) % n);
+  const int k = (int)(t / ((long long)n * n));
+  const double sc = -0.25 * (double)n;  // -(1/2) / (2h)
+  out[t] = sc * (phi[lidx(wrap_up(i, n), j, k, n)] - phi[lidx(wrap_dn(i, n), j, k, n)]);
+  out[cells + t] = sc * (phi[lidx(i, wrap_up(j, n), k, n)] - phi[lidx(i, wrap_dn(j, n), k, n)]);
+  out[2 * cells + t] = sc * (phi[lidx(i, j, wrap_up(k, n), n)] - phi[lidx(i, j, wrap_dn(k, n), n)]);
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+static inline unsigned blocks_for(long long work, int threads) {
+  return (unsigned)((work + threads - 1) / threads);
+}
+
+OpConst64 make_op64(int n, double alpha, double kappa, int branch) {
+  OpConst64 c{};
+  const double h = 1.0 / (double)n;
+  const double w = 1.0 / 3.0;
+  c.h2 = h * h;
+  c.inv_h2 = (double)n * (double)n;
+  const double h4 = c.h2 * c.h2;
+  c.c3 = 4.0 * (1.0 - w) * alpha;
+  if (alpha == 0.0) {
+    c.mode = OP_LINEAR;
+    return c;
+  }
+  const double sigma = (branch == 0) ? 1.0 : ((branch > 0) == (alpha > 0) ? 1.0 : -1.0);
+  c.k2 = 2.0 / c.c3;
+  c.k2s = sigma * c.k2;
+  c.c1 = alpha / (3.0 * h4);
+  c.c2 = alpha / (8.0 * h4);
+  c.e1 = c.c3 * c.c1;
+  c.e2 = c.c3 * c.c2;
+  // k2 (sigma sqrt(q) - 1) loses about |k2| * eps to cancellation on the physical
+  // root; below |alpha| = 1e-4 the conjugate form 2u/(1+sqrt q) is used instead.
+  c.mode = (sigma > 0 && fabs(alpha) < 1e-4) ? OP_CONJ : OP_SQRT;
+  return c;
+}
+
+void src_coefficients(const OpConst64& c, double kappa, double* a, double* b) {
+  if (c.mode == OP_SQRT) {
+    *a = c.c3 * kappa;
+    *b = 1.0;
+  } else {
+    *a = kappa;
+    *b = 0.0;
+  }
+}
+
+thread_local long long tl_launches = 0;
+
+void launch_smooth64(cudaStream_t st, int n, double* phi, const double* src, const double* f,
+                     const LevelScalars* sc, const OpConst64& c, int sweeps, EventPairs* timer) {
+  const long long per = (long long)(n / 2) * (n / 2) * n;
+  for (int s = 0; s < sweeps; ++s)
+    for (int colour = 0; colour < 4; ++colour) {
+      if (timer) timer->begin(st);
+      k_smooth_colour64<<<blocks_for(per, 256), 256, 0, st>>>(n, phi, src, f, sc, c, colour);
+      if (timer) timer->end(st);
+    }
+  count_launches(4LL * sweeps);
+}
+
+int partials_needed(long long cells) { return (int)blocks_for(cells, 128) + 1; }
+
+void launch_residual64(cudaStream_t st, int n, const double* phi, const double* src,
+                       const double* f, double* dout, const OpConst64& c, Partial* partials,
+                       LevelScalars* sc, int periodic) {
+  const long long cells = (long long)n * n * n;
+  const unsigned nb = blocks_for(cells, 256);
+  k_residual64<<<nb, 256, 0, st>>>(n, phi, src, f, dout, c, partials);
+  k_finalize<<<1, 256, 0, st>>>(partials, (int)nb, (double)cells, periodic, sc);
+  count_launches(2);
+}
+
+void launch_residual_restrict64(cudaStream_t st, int nf, const double* phi, const double* src,
+                                const double* f, const OpConst64& c, double* phi_c,
+                                double* phihat_c, double* rd_c, Partial* partials,
+                                LevelScalars* sc) {
+  const long long ccells = (long long)(nf / 2) * (nf / 2) * (nf / 2);
+  const unsigned nb = blocks_for(ccells, 128);
+  k_residual_restrict64<<<nb, 128, 0, st>>>(nf, phi, src, f, c, phi_c, phihat_c, rd_c, partials);
+  k_finalize<<<1, 256, 0, st>>>(partials, (int)nb, (double)nf * nf * nf, 1, sc);
+  count_launches(2);
+}
+
+void launch_fas_rhs64(cudaStream_t st, int nc, const double* phi_c, const double* src_c,
+                      double* f_c, const OpConst64& c, const LevelScalars* fine_sc,
+                      LevelScalars* coarse_sc) {
+  const long long cells = (long long)nc * nc * nc;
+  k_fas_rhs64<<<blocks_for(cells, 256), 256, 0, st>>>(nc, phi_c, src_c, f_c, c, fine_sc,
+                                                      coarse_sc);
+  count_launches(1);
+}
+
+void launch_prolong_correct64(cudaStream_t st, int nc, const double* phi_c,
+                              const double* phihat_c, double* phi_f) {
+  const long long cells = 8LL * nc * nc * nc;
+  k_prolong_correct64<<<blocks_for(cells, 256), 256, 0, st>>>(nc, phi_c, phihat_c, phi_f);
+  count_launches(1);
+}
+
+void launch_coarsest64(cudaStream_t st, int n, double* phi, const double* src, const double* f,
+                       const OpConst64& c, LevelScalars* sc, int max_sweeps, double drop) {
+  const size_t smem = 3 * sizeof(double) * (size_t)n * n * n;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_coarsest64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         3 * sizeof(double) * 4096);
+    attr_set = true;
+  }
+  k_coarsest64<<<1, 256, smem, st>>>(n, phi, src, f, c, sc, max_sweeps, drop, 2);
+  count_launches(1);
+}
+
+void launch_restrict64(cudaStream_t st, int nc, const double* fine, double* coarse) {
+  const long long cells = (long long)nc * nc * nc;
+  k_restrict64<<<blocks_for(cells, 256), 256, 0, st>>>(nc, fine, coarse);
+  count_launches(1);
+}
+
+void launch_affine64(cudaStream_t st, long long cells, const double* x, double* out, double a,
+                     double b, double c3, int floor, unsigned long long* floored) {
+  k_affine64<<<blocks_for(cells, 256), 256, 0, st>>>(cells, x, out, a, b, c3, floor, floored);
+  count_launches(1);
+}
+
+void launch_gauge64(cudaStream_t st, long long cells, double* x, Partial* partials,
+                    LevelScalars* sc) {
+  const unsigned nb = blocks_for(cells, 256);
+  k_sum_partials<<<nb, 256, 0, st>>>(cells, x, partials);
+  k_finalize<<<1, 256, 0, st>>>(partials, (int)nb, (double)cells, 1, sc);
+  k_sub_mean<<<nb, 256, 0, st>>>(cells, x, sc);
+  count_launches(3);
+}
+
+void launch_force64(cudaStream_t st, int n, const double* phi, double* out) {
+  const long long cells = (long long)n * n * n;
+  k_force64<<<blocks_for(cells, 256), 256, 0, st>>>(n, phi, out);
+  count_launches(1);
+}
+
+}  // namespace mg
+
+namespace mg {
+void launch_finalize(cudaStream_t st, const Partial* partials, int nparts, double cells,
+                     int periodic, LevelScalars* sc) {
+  k_finalize<<<1, 256, 0, st>>>(partials, nparts, cells, periodic, sc);
+  count_launches(1);
+}
+}  // namespace mg

@@ -1,0 +1,116 @@
+// Host-side declarations shared by the translation units of libmg.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "mg_common.cuh"
+
+namespace mg {
+
+void set_error(const std::string& msg);
+
+// Kernel launches issued by this thread (graph captures included).
+extern thread_local long long tl_launches;
+inline void count_launches(long long k) { tl_launches += k; }
+
+// CUDA event pairs around individual kernel launches on one stream; while the
+// stream is being captured the records become external event nodes of the graph.
+struct EventPairs {
+  std::vector<cudaEvent_t> start, stop;
+  int n = 0;
+  bool capturing = false;
+  bool enabled = false;
+  ~EventPairs() {
+    for (auto e : start) cudaEventDestroy(e);
+    for (auto e : stop) cudaEventDestroy(e);
+  }
+  void begin(cudaStream_t st) {
+    if (!enabled) return;
+    if ((int)start.size() <= n) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      start.push_back(a);
+      stop.push_back(b);
+    }
+    if (capturing) cudaEventRecordWithFlags(start[n], st, cudaEventRecordExternal);
+    else cudaEventRecord(start[n], st);
+  }
+  void end(cudaStream_t st) {
+    if (!enabled) return;
+    if (capturing) cudaEventRecordWithFlags(stop[n], st, cudaEventRecordExternal);
+    else cudaEventRecord(stop[n], st);
+    ++n;
+  }
+  // Summed milliseconds of the recorded pairs (their work must have completed).
+  double read_ms() const {
+    double total = 0.0;
+    for (int i = 0; i < n; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, start[i], stop[i]) == cudaSuccess) total += ms;
+    }
+    return total;
+  }
+};
+
+// Capture `body` as a graph; *launches receives the kernels it holds (they are
+// not counted as issued until the graph is launched).
+template <typename F>
+inline cudaGraphExec_t capture_graph(cudaStream_t st, long long* launches, const F& body) {
+  cudaGraph_t graph = nullptr;
+  const long long before = tl_launches;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  body();
+  *launches = tl_launches - before;
+  tl_launches = before;
+  if (cudaStreamEndCapture(st, &graph) != cudaSuccess || !graph) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    exec = nullptr;
+  }
+  cudaGraphDestroy(graph);
+  return exec;
+}
+
+// ---- FP64 periodic kernels (mg_fp64.cu) ----
+OpConst64 make_op64(int n, double alpha, double kappa, int branch);
+void src_coefficients(const OpConst64& c, double kappa, double* a, double* b);
+int partials_needed(long long cells);
+void launch_smooth64(cudaStream_t st, int n, double* phi, const double* src, const double* f,
+                     const LevelScalars* sc, const OpConst64& c, int sweeps,
+                     EventPairs* timer = nullptr);
+void launch_finalize(cudaStream_t st, const Partial* partials, int nparts, double cells,
+                     int periodic, LevelScalars* sc);
+void launch_residual64(cudaStream_t st, int n, const double* phi, const double* src,
+                       const double* f, double* dout, const OpConst64& c, Partial* partials,
+                       LevelScalars* sc, int periodic);
+void launch_residual_restrict64(cudaStream_t st, int nf, const double* phi, const double* src,
+                                const double* f, const OpConst64& c, double* phi_c,
+                                double* phihat_c, double* rd_c, Partial* partials,
+                                LevelScalars* sc);
+void launch_fas_rhs64(cudaStream_t st, int nc, const double* phi_c, const double* src_c,
+                      double* f_c, const OpConst64& c, const LevelScalars* fine_sc,
+                      LevelScalars* coarse_sc);
+void launch_prolong_correct64(cudaStream_t st, int nc, const double* phi_c,
+                              const double* phihat_c, double* phi_f);
+void launch_coarsest64(cudaStream_t st, int n, double* phi, const double* src, const double* f,
+                       const OpConst64& c, LevelScalars* sc, int max_sweeps, double drop);
+void launch_restrict64(cudaStream_t st, int nc, const double* fine, double* coarse);
+void launch_affine64(cudaStream_t st, long long cells, const double* x, double* out, double a,
+                     double b, double c3 = 0.0, int floor = 0,
+                     unsigned long long* floored = nullptr);
+void launch_gauge64(cudaStream_t st, long long cells, double* x, Partial* partials,
+                    LevelScalars* sc);
+void launch_force64(cudaStream_t st, int n, const double* phi, double* out);
+
+}  // namespace mg

@@ -1,0 +1,119 @@
+// Host-side state of libmg: the periodic level hierarchy of one domain, the
+// refinement patch levels, and the batch work lists.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_common.cuh"
+
+namespace mg {
+
+// One multigrid level of a periodic domain (dense n^3 arrays, x fastest).
+struct Level {
+  int n = 0;
+  long long cells = 0;
+  double* phi = nullptr;     // field
+  double* delta = nullptr;   // density contrast (restricted from the finest level)
+  double* src = nullptr;     // per-solve source term of the operator
+  double* f = nullptr;       // FAS right-hand side (coarse levels)
+  double* phihat = nullptr;  // R phi^h kept for the correction (coarse levels)
+  // mixed precision (FP32 correction operator), allocated on first use
+  float* e = nullptr;        // correction
+  float* ehat = nullptr;     // R e kept for the correction (coarse levels)
+  float* phi0 = nullptr;     // FP32 copy of the expansion point
+  float* q0 = nullptr;       // discriminant at the expansion point
+  float* rhs = nullptr;      // right-hand side of N(e) = rhs (+ mu)
+  float* src32 = nullptr;    // kappa * delta in FP32 (coarse levels)
+};
+
+struct Domain {
+  int n = 0;
+  int nlev = 0;
+  std::vector<Level> lv;
+  LevelScalars* d_sc = nullptr;  // 2 * nlev + 2 entries (FP64 levels, FP32 levels, spare)
+  LevelScalars* h_sc = nullptr;  // pinned mirror of d_sc[0] and d_sc[nlev]
+  Partial* d_part = nullptr;
+  int part_cap = 0;
+  bool density_set = false;
+  bool mixed_ready = false;
+  // CUDA graphs of the two halves of a V-cycle (captured per solve)
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+// One refinement level: 8^3 patches (Sec. III.C, first paragraph).
+struct PatchLevel {
+  int level = 0;       // 1 or 2
+  int count = 0;
+  int nside = 0;       // cells per side of this level's periodic index space
+  bool density_set = false;
+  int* d_origin = nullptr;    // 3 * count
+  int* d_nbr = nullptr;       // 27 * count: neighbour patch index or -1
+  double* phi = nullptr;      // count * 512
+  double* delta = nullptr;
+  double* src = nullptr;
+  double* ghost = nullptr;    // count * 1000 ghosted blocks: Dirichlet fill
+  std::vector<int> h_origin;
+  // union multigrid: coarse levels of the patch union (4^3 and 2^3 per patch)
+  double* phi_c[3] = {nullptr, nullptr, nullptr};
+  double* phihat_c[3] = {nullptr, nullptr, nullptr};
+  double* f_c[3] = {nullptr, nullptr, nullptr};
+  double* src_c[3] = {nullptr, nullptr, nullptr};
+  double* delta_c[3] = {nullptr, nullptr, nullptr};
+  double* ghost_c[3] = {nullptr, nullptr, nullptr};
+  LevelScalars* d_sc = nullptr;
+  LevelScalars* h_sc = nullptr;
+  Partial* d_part = nullptr;
+  int part_cap = 0;
+  int* d_table = nullptr;           // (nside/8)^3 block -> patch index or -1
+  int* d_err = nullptr;             // set when a Dirichlet value finds no parent cell
+  double* d_coarse_parent = nullptr;  // level 1: the domain field restricted once
+  int last_cycles = 0;
+  double last_res = 0.0;
+};
+
+struct BatchState;
+
+}  // namespace mg
+
+struct mg_grid {
+  mg_options opt;
+  std::vector<mg::Domain*> domains;
+  bool batch = false;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;
+  std::vector<mg::PatchLevel*> patch_levels;
+  double* force_tmp = nullptr;
+  size_t force_tmp_bytes = 0;
+  mg::BatchState* bs = nullptr;
+};
+
+namespace mg {
+
+// mg_domain.cu
+mg_status domain_create(Domain** out, int n, const mg_options& o);
+void domain_destroy(Domain* d);
+void domain_invalidate_graphs(Domain* d);
+void domain_restrict_density(Domain* d, cudaStream_t st);
+mg_status domain_solve(Domain* d, const mg_options& o, cudaStream_t st, int branch, double alpha,
+                       double kappa, double tol, mg_solve_stats* stats);
+int num_levels(int n, int coarsest);
+
+// mg_patch.cu
+mg_status patches_add(mg_grid* g, int level, int count, const int* origin);
+void patch_level_destroy(PatchLevel* pl);
+mg_status patch_level_solve(mg_grid* g, int level, int branch, double alpha, double kappa,
+                            double tol);
+mg_status patch_force(mg_grid* g, int level, int patch, double* out);
+void patch_restrict_density(mg_grid* g, PatchLevel* pl);
+
+// mg_batch.cu
+mg_status batch_prepare(mg_grid* g);
+void batch_release(mg_grid* g);
+mg_status batch_solve(mg_grid* g, const int* branch, const double* alpha, const double* kappa,
+                      double tol, mg_solve_stats* stats);
+
+}  // namespace mg

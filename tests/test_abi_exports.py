@@ -1,0 +1,58 @@
+"""The C-ABI library builds, loads and exports every symbol include/mg.h declares.
+No compute call is made (no GPU needed)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mg.h")
+
+
+def declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1303_0008_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for required in ["mg_create_grid", "mg_set_density", "mg_solve", "mg_get_field",
+                     "mg_get_force", "mg_destroy_grid", "mg_last_error", "mg_add_patches",
+                     "mg_set_field", "mg_create_batch", "mg_solve_batch"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (mg_[a-z_0-9]+)\b", out))
+    missing = [n for n in declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_ctypes_binding_covers_the_header(libpath):
+    from paper_1303_0008_gb300 import mg
+    L = mg.lib()
+    for name in declared():
+        assert hasattr(L, name)
+    assert set(mg.exported_symbols()) == set(declared())
+
+
+def test_binding_rejects_bad_arguments_without_gpu(libpath):
+    from paper_1303_0008_gb300 import mg
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_create_grid(7)
+    assert e.value.status == mg.MG_EINVAL
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_create_grid(36)          # coarsest side 18 > 16
+    assert e.value.status == mg.MG_EINVAL
+    with pytest.raises(mg.MGError):
+        mg.options(nu_pre=0, nu_post=0) and mg.mg_create_grid(8, mg.options(nu_pre=0, nu_post=0))

@@ -540,3 +540,50 @@ def test_multilevel_tophat_refinement_improves_accuracy():
     e_int = np.abs(cut(interp) - cut(phif)).max()
     assert e_ref < 0.3 * e_int
     assert e_ref < 0.03 * (phif.max() - phif.min())
+
+
+# ---------------------------------------------------------------------------
+# source floor (the reading used where alpha*kappa*delta < -3/8)
+# ---------------------------------------------------------------------------
+def test_density_floor_bound_and_symmetry():
+    delta = I.lognormal_delta(16, 1.5, 1302)
+    a = I.alpha_kappa_for_rv(32.0)
+    fl, hits = O.density_floor(delta, a, 1.0)
+    assert hits == int((1 + 4 * (1 - W) * a * delta < 0).sum()) > 0
+    assert (1 + 4 * (1 - W) * a * fl >= -1e-12).all()
+    assert np.array_equal(fl[fl != delta], np.full(hits, -1 / (4 * (1 - W) * a)))
+    fl2, hits2 = O.density_floor(delta, -a, -1.0)        # flipping beta: same cells
+    assert hits2 == hits and np.array_equal(fl, fl2)
+    same, none = O.density_floor(delta, I.alpha_kappa_for_rv(8.0), 1.0)   # alpha*kappa < 3/8
+    assert none == 0 and np.array_equal(same, delta)
+
+
+def test_floored_system_has_no_imaginary_root_and_matches_brute_force():
+    """With the floor, the discriminant is non-negative for any field: the solve sees no
+    guarded cell, and brute-force Newton on the unsplit bordered 8^3 system agrees."""
+    n = 8
+    rng = np.random.default_rng(82)
+    delta = rng.uniform(-1.0, 2.0, size=(n, n, n))
+    delta -= delta.mean()
+    alpha = 2.4
+    fl, hits = O.density_floor(delta, alpha, 1.0)
+    assert hits > 20
+    phi, st = O.fas_solve(fl, alpha, 1.0, tol=1e-12, max_cycles=200)
+    assert st["status"] == O.OK and st["guard_hits"] == 0
+    x = newton_bordered(fl, alpha, 1.0, n, 8)
+    G, q, D = bordered_residual(x, fl, alpha, 1.0, 1.0 / n, n)
+    assert np.abs(G).max() < 1e-10 and (q >= 0).all()
+    assert max_rel(phi, x[:-1].reshape(n, n, n)) < 1e-9
+
+
+def test_floor_makes_the_strong_screening_case_converge():
+    """r_V = 32 cells (alpha*kappa = 19.2) on the 32^3 lognormal field: with the
+    real-part reading alone the Newton-Gauss-Seidel iteration cycles; with the floor
+    it converges."""
+    delta = I.lognormal_delta(32, 1.5, 1302)
+    a = I.alpha_kappa_for_rv(32.0)
+    _, st_root = O.fas_solve(delta, a, 1.0, tol=1e-10, max_cycles=40)
+    assert st_root["status"] != O.OK and st_root["res"] > 1e-4
+    fl, hits = O.density_floor(delta, a, 1.0)
+    _, st = O.fas_solve(fl, a, 1.0, tol=1e-10, max_cycles=60)
+    assert st["status"] == O.OK and st["guard_hits"] == 0
