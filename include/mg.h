@@ -234,6 +234,7 @@ mg_status mg_op_prolong_correct(int n, const double* coarse, const double* coars
 /* out[3 n^3] = -(1/2) grad phi. */
 mg_status mg_op_force(int n, const double* phi, double* out, void* stream);
 
+
 #ifdef __cplusplus
 }
 #endif
