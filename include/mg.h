@@ -234,6 +234,26 @@ mg_status mg_op_prolong_correct(int n, const double* coarse, const double* coars
 /* out[3 n^3] = -(1/2) grad phi. */
 mg_status mg_op_force(int n, const double* phi, double* out, void* stream);
 
+/*
+ * mg_op_residual without any device allocation (the paper has no counterpart:
+ * it is a service to callers).  mg_op_residual allocates and frees temporaries
+ * with cudaMalloc/cudaFree on every call; those calls synchronise the whole
+ * device, and they fail in a process whose device memory is already taken by
+ * its own allocator.  Callers in that position (programs that overlap work on
+ * several streams, or that hand the card to a framework's memory pool) use this
+ * entry point instead.  Same arguments, same results as mg_op_residual.
+ *   - Limit: n <= 256 (at most 256^3 cells); larger n returns MG_EINVAL.
+ *   - Storage: a fixed, file-scope device array of about 2.6 MB that every device
+ *     loading the library holds until the process ends.  All calls on a device
+ *     share it and it keeps the last call's contents; calls that overlap on the
+ *     GPU race on it, so the caller must order them (one stream, or events).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Errors: MG_EINVAL (size, branch, NULL input), MG_ECUDA.
+ */
+mg_status mg_op_residual_noalloc(int n, const double* phi, const double* delta, const double* f,
+                                 int branch, double alpha, double kappa, double* d, double* norms,
+                                 void* stream);
 
 #ifdef __cplusplus
 }

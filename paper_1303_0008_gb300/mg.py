@@ -83,6 +83,7 @@ _SIGS = {
     "mg_op_restrict": (_I, [_I, _P, _P, _P]),
     "mg_op_prolong_correct": (_I, [_I, _P, _P, _P, _P]),
     "mg_op_force": (_I, [_I, _P, _P, _P]),
+    "mg_op_residual_noalloc": (_I, [_I, _P, _P, _P, _I, _F, _F, _P, _D, _P]),
 }
 
 
@@ -258,6 +259,15 @@ def mg_op_restrict(n, fine, coarse, stream=None):
 def mg_op_prolong_correct(n, coarse, coarse_ref, fine, stream=None):
     _check(lib().mg_op_prolong_correct(n, _dev(coarse), _dev(coarse_ref), _dev(fine),
                                        _stream(stream)), "mg_op_prolong_correct")
+
+
+def mg_op_residual_noalloc(n, phi, delta, f, branch, alpha, kappa, d=None, stream=None):
+    """mg_op_residual for callers that cannot allocate device memory (n <= 256)."""
+    norms = (ctypes.c_double * 5)()
+    _check(lib().mg_op_residual_noalloc(n, _dev(phi), _dev(delta), _dev(f), branch, alpha, kappa,
+                                        _dev(d), norms, _stream(stream)), "mg_op_residual_noalloc")
+    return {"sum": norms[0], "max": norms[1], "min": norms[2], "guards": int(norms[3]),
+            "nonfinite": int(norms[4])}
 
 
 def mg_op_force(n, phi, out, stream=None):
