@@ -96,6 +96,8 @@ typedef struct {
   mg_guard guard;    /* default MG_GUARD_FLOOR */
   int patch_coarse_sweeps; /* sweeps on the coarsest (2^3 per patch) level of a
                               refinement union per V-cycle (default 8) */
+  int fuse_coarse;   /* 1: run the levels with <= 16 cells per side, down to the
+                        coarsest, as one launch of a thread-block cluster (default 1) */
 } mg_options;
 
 typedef struct {

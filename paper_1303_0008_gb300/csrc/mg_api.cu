@@ -57,6 +57,7 @@ void mg_default_options(mg_options* opt) {
   opt->time_kernels = 0;
   opt->guard = MG_GUARD_FLOOR;
   opt->patch_coarse_sweeps = 8;
+  opt->fuse_coarse = 1;
 }
 
 static mg_status check_options(const mg_options& o) {
@@ -72,6 +73,7 @@ static mg_status check_options(const mg_options& o) {
   if (o.guard != MG_GUARD_FLOOR && o.guard != MG_GUARD_ROOT) MG_FAIL(MG_EINVAL, "options: guard");
   if (o.patch_coarse_sweeps < 1 || o.patch_coarse_sweeps > 10000)
     MG_FAIL(MG_EINVAL, "options: patch_coarse_sweeps");
+  if (o.fuse_coarse != 0 && o.fuse_coarse != 1) MG_FAIL(MG_EINVAL, "options: fuse_coarse");
   return MG_OK;
 }
 

@@ -1,0 +1,333 @@
+// Per-thread bodies of the mixed-precision kernels of mg_mixed.cu (see
+// mg_bodies64.cuh for the convention).
+#pragma once
+
+#include "mg_common.cuh"
+
+namespace mg {
+
+// The change of the root D when phi0 moves by e, from the stencils of e and phi0.
+template <typename T>
+__device__ __forceinline__ T delta_D(const StencilT<T>& se, const StencilT<T>& sp, T q0, T g1,
+                                     T g2, T c3, T k2, T sigma, T& du_out) {
+  const T a1e = se.sx - se.sy, a2e = se.sx - se.sz, a3e = se.sy - se.sz;
+  const T a1p = sp.sx - sp.sy, a2p = sp.sx - sp.sz, a3p = sp.sy - sp.sz;
+  const T two = T(2);
+  const T dA = a1e * (two * a1p + a1e) + a2e * (two * a2p + a2e) + a3e * (two * a3p + a3e);
+  const T dB = se.cxy * (two * sp.cxy + se.cxy) + se.cxz * (two * sp.cxz + se.cxz) +
+               se.cyz * (two * sp.cyz + se.cyz);
+  const T du = g1 * dA + g2 * dB;
+  du_out = du;
+  const T q1 = q0 + c3 * du;
+  const T s0 = sqrt(q0 > T(0) ? q0 : T(0));
+  const T s1 = sqrt(q1 > T(0) ? q1 : T(0));
+  if (q0 >= T(0) && q1 >= T(0)) {
+    const T den = s0 + s1;
+    return den > T(0) ? sigma * two * du / den : T(0);
+  }
+  return sigma * k2 * (s1 - s0);
+}
+
+__device__ __forceinline__ float dD32(const StencilT<float>& se, const StencilT<float>& sp,
+                                      float q0, const OpConst32& c) {
+  if (c.linear) return 0.f;
+  float du;
+  return delta_D<float>(se, sp, q0, c.g1, c.g2, c.c3, c.k2, c.sigma, du);
+}
+
+__device__ __forceinline__ void b_residual_handoff64(
+    int n, const double* __restrict__ phi, const double* __restrict__ src, OpConst64 c,
+    const LevelScalars* __restrict__ sc, float* __restrict__ g, float* __restrict__ q0,
+    float* __restrict__ phi0, float* __restrict__ e, Partial* __restrict__ partials,
+    long long blk) {
+  const long long cells = (long long)n * n * n;
+  const long long t = (long long)blk * blockDim.x + threadIdx.x;
+  Partial p;
+  partial_init(p);
+  if (t < cells) {
+    const int i = (int)(t % n);
+    const int j = (int)((t / n) % n);
+    const int k = (int)(t / ((long long)n * n));
+    const StencilT<double> s = gather_periodic(phi, i, j, k, n);
+    double q = 1.0, D;
+    bool guard = false;
+    if (c.mode == OP_LINEAR) {
+      D = src[t];
+    } else {
+      const double A2 = half_A(s);
+      const double B = fma(s.cxy, s.cxy, fma(s.cxz, s.cxz, s.cyz * s.cyz));
+      if (c.mode == OP_SQRT) {
+        q = fma(c.e1h, A2, fma(c.e2, B, src[t]));
+        D = fma(c.k2s, sqrt_nonneg(q < 0.0 ? 0.0 : q), -c.k2);
+      } else {
+        const double u = fma(c.c1h, A2, fma(c.c2, B, src[t]));
+        q = fma(c.c3, u, 1.0);
+        D = (q < 0.0) ? -c.k2 : (2.0 * u) / (1.0 + sqrt(q));
+      }
+      guard = q < 0.0;
+    }
+    const double ctr = phi[t];
+    const double lap = (s.sx + s.sy + s.sz) - 6.0 * ctr;
+    const double d = fma(lap, c.inv_h2, -D);
+    partial_add(p, d, guard);
+    g[t] = (float)(sc->lambda - d);
+    q0[t] = (float)q;
+    phi0[t] = (float)ctr;
+    e[t] = 0.f;
+  }
+  p = block_reduce(p);
+  if (threadIdx.x == 0) partials[blk] = p;
+}
+
+__device__ __forceinline__ void b_update64(long long cells, double* __restrict__ phi,
+                                                  const float* __restrict__ e,
+    long long blk) {
+  const long long t = (long long)blk * blockDim.x + threadIdx.x;
+  if (t < cells) phi[t] += (double)e[t];
+}
+
+__device__ __forceinline__ void b_restrict32(int nc, const float* __restrict__ fine,
+                                                    float* __restrict__ coarse,
+    long long blk) {
+  const int nf = nc << 1;
+  const long long cells = (long long)nc * nc * nc;
+  const long long t = (long long)blk * blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  const int I = (int)(t % nc);
+  const int J = (int)((t / nc) % nc);
+  const int K = (int)(t / ((long long)nc * nc));
+  float s = 0.f;
+#pragma unroll
+  for (int ch = 0; ch < 8; ++ch)
+    s += fine[lidx(2 * I + (ch & 1), 2 * J + ((ch >> 1) & 1), 2 * K + (ch >> 2), nf)];
+  coarse[t] = s * 0.125f;
+}
+
+__device__ __forceinline__ void b_q0_prep32(int n, const float* __restrict__ phi0,
+                                                   const double* __restrict__ delta,
+                                                   OpConst32 c, float kappa, int floor,
+                                                   float* __restrict__ q0,
+    long long blk) {
+  const long long cells = (long long)n * n * n;
+  const long long t = (long long)blk * blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  if (c.linear) {
+    q0[t] = 1.f;
+    return;
+  }
+  const int i = (int)(t % n);
+  const int j = (int)((t / n) % n);
+  const int k = (int)(t / ((long long)n * n));
+  const StencilT<float> s = gather_periodic(phi0, i, j, k, n);
+  const float a1 = s.sx - s.sy, a2 = s.sx - s.sz, a3 = s.sy - s.sz;
+  const float A = a1 * a1 + a2 * a2 + a3 * a3;
+  const float B = s.cxy * s.cxy + s.cxz * s.cxz + s.cyz * s.cyz;
+  float qs = fmaf(c.c3 * kappa, (float)delta[t], 1.f);
+  if (floor && qs < 0.f) qs = 0.f;
+  q0[t] = fmaf(c.c3, c.g1 * A + c.g2 * B, qs);
+}
+
+__device__ __forceinline__ void b_smooth_colour32(int n, float* __restrict__ e,
+                                                         const float* __restrict__ phi0,
+                                                         const float* __restrict__ q0,
+                                                         const float* __restrict__ g,
+                                                         const LevelScalars* __restrict__ sc,
+                                                         OpConst32 c, int colour,
+    long long blk) {
+  const int hn = n >> 1;
+  const long long t = (long long)blk * blockDim.x + threadIdx.x;
+  const long long total = (long long)hn * hn * n;
+  if (t >= total) return;
+  const int m = (int)(t % hn);
+  const long long rest = t / hn;
+  const int jj = (int)(rest % hn);
+  const int k = (int)(rest / hn);
+  const int i = 2 * m + ((colour ^ k) & 1);
+  const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
+  const long long id = lidx(i, j, k, n);
+  const StencilT<float> se = gather_periodic(e, i, j, k, n);
+  float dd = 0.f;
+  if (!c.linear) {
+    const StencilT<float> sp = gather_periodic(phi0, i, j, k, n);
+    dd = dD32(se, sp, q0[id], c);
+  }
+  const float rhs = g[id] + (float)sc->lambda;
+  e[id] = fmaf(-c.h2, dd + rhs, se.sx + se.sy + se.sz) * (1.f / 6.f);
+}
+
+__device__ __forceinline__ void b_residual_restrict32(
+    int nf, const float* __restrict__ e, const float* __restrict__ phi0,
+    const float* __restrict__ q0, const float* __restrict__ g, OpConst32 c,
+    float* __restrict__ e_c, float* __restrict__ ehat_c, float* __restrict__ rg_c,
+    Partial* __restrict__ partials,
+    long long blk) {
+  const int nc = nf >> 1;
+  const long long ccells = (long long)nc * nc * nc;
+  const long long t = (long long)blk * blockDim.x + threadIdx.x;
+  Partial p;
+  partial_init(p);
+  if (t < ccells) {
+    const int I = (int)(t % nc);
+    const int J = (int)((t / nc) % nc);
+    const int K = (int)(t / ((long long)nc * nc));
+    float se_sum = 0.f, sr = 0.f;
+#pragma unroll 1
+    for (int ch = 0; ch < 8; ++ch) {
+      const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
+      const long long id = lidx(i, j, k, nf);
+      const StencilT<float> se = gather_periodic(e, i, j, k, nf);
+      float dd = 0.f;
+      if (!c.linear) {
+        const StencilT<float> sp = gather_periodic(phi0, i, j, k, nf);
+        dd = dD32(se, sp, q0[id], c);
+      }
+      const float ctr = e[id];
+      const float lap = (se.sx + se.sy + se.sz) - 6.f * ctr;
+      const float r = fmaf(lap, c.inv_h2, -dd) - g[id];
+      partial_add(p, (double)r, false);
+      se_sum += ctr;
+      sr += r;
+    }
+    e_c[t] = se_sum * 0.125f;
+    ehat_c[t] = se_sum * 0.125f;
+    rg_c[t] = sr * 0.125f;
+  }
+  p = block_reduce(p);
+  if (threadIdx.x == 0) partials[blk] = p;
+}
+
+__device__ __forceinline__ void b_fas_rhs32(int nc, const float* __restrict__ e_c,
+                                                   const float* __restrict__ phi0_c,
+                                                   const float* __restrict__ q0_c,
+                                                   float* __restrict__ g_c, OpConst32 c,
+                                                   const LevelScalars* __restrict__ fine_sc,
+                                                   LevelScalars* __restrict__ coarse_sc,
+    long long blk) {
+  const long long cells = (long long)nc * nc * nc;
+  const long long t = (long long)blk * blockDim.x + threadIdx.x;
+  if (t == 0) coarse_sc->lambda = 0.0;
+  if (t >= cells) return;
+  const int i = (int)(t % nc);
+  const int j = (int)((t / nc) % nc);
+  const int k = (int)(t / ((long long)nc * nc));
+  const StencilT<float> se = gather_periodic(e_c, i, j, k, nc);
+  float dd = 0.f;
+  if (!c.linear) {
+    const StencilT<float> sp = gather_periodic(phi0_c, i, j, k, nc);
+    dd = dD32(se, sp, q0_c[t], c);
+  }
+  const float lap = (se.sx + se.sy + se.sz) - 6.f * e_c[t];
+  const float Nv = fmaf(lap, c.inv_h2, -dd);
+  g_c[t] = Nv - g_c[t] + (float)fine_sc->lambda;
+}
+
+__device__ __forceinline__ void b_prolong_correct32(int nc, const float* __restrict__ e_c,
+                                                           const float* __restrict__ ehat_c,
+                                                           float* __restrict__ e_f,
+    long long blk) {
+  const int nf = nc << 1;
+  const long long cells = (long long)nf * nf * nf;
+  const long long t = (long long)blk * blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  const int i = (int)(t % nf);
+  const int j = (int)((t / nf) % nf);
+  const int k = (int)(t / ((long long)nf * nf));
+  const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+  const int I1 = (i & 1) ? wrap_up(I0, nc) : wrap_dn(I0, nc);
+  const int J1 = (j & 1) ? wrap_up(J0, nc) : wrap_dn(J0, nc);
+  const int K1 = (k & 1) ? wrap_up(K0, nc) : wrap_dn(K0, nc);
+  auto v = [&](int a, int b, int cc) {
+    const long long q = lidx(a, b, cc, nc);
+    return e_c[q] - ehat_c[q];
+  };
+  const float s = 27.f * v(I0, J0, K0) + 9.f * (v(I1, J0, K0) + v(I0, J1, K0) + v(I0, J0, K1)) +
+                  3.f * (v(I1, J1, K0) + v(I1, J0, K1) + v(I0, J1, K1)) + v(I1, J1, K1);
+  e_f[t] += s * (1.f / 64.f);
+}
+
+__device__ __forceinline__ void b_coarsest_corr64(int n, float* __restrict__ e,
+                                                         const float* __restrict__ phi0,
+                                                         const float* __restrict__ q0,
+                                                         const float* __restrict__ g, OpConst32 c,
+                                                         LevelScalars* __restrict__ sc,
+                                                         int max_sweeps, double drop,
+    long long blk) {
+  extern __shared__ double smc[];
+  __shared__ double s_mu, s_res0, s_res;
+  const int cells = n * n * n;
+  double* se = smc;
+  double* sp = smc + cells;
+  double* sq = smc + 2 * cells;
+  double* sg = smc + 3 * cells;
+  for (int q = threadIdx.x; q < cells; q += blockDim.x) {
+    se[q] = e[q];
+    sp[q] = phi0[q];
+    sq[q] = q0[q];
+    sg[q] = g[q];
+  }
+  if (threadIdx.x == 0) s_mu = sc->lambda;
+  __syncthreads();
+  const double h2 = (double)c.h2, inv_h2 = (double)c.inv_h2;
+  const double g1 = (double)c.g1, g2 = (double)c.g2, c3 = (double)c.c3, k2 = (double)c.k2,
+               sigma = (double)c.sigma;
+  auto ddv = [&](const StencilT<double>& a, const StencilT<double>& b, double qq) {
+    if (c.linear) return 0.0;
+    double du;
+    return delta_D<double>(a, b, qq, g1, g2, c3, k2, sigma, du);
+  };
+  double scale = 0.0;
+  auto residual = [&]() {
+    Partial p;
+    partial_init(p);
+    double mag = 0.0;
+    for (int q = threadIdx.x; q < cells; q += blockDim.x) {
+      const int i = q % n, j = (q / n) % n, k = q / (n * n);
+      const StencilT<double> a = gather_periodic<double>(se, i, j, k, n);
+      const StencilT<double> b = gather_periodic<double>(sp, i, j, k, n);
+      const double lnb = a.sx + a.sy + a.sz;
+      const double lap = lnb - 6.0 * se[q];
+      const double dd = ddv(a, b, sq[q]);
+      partial_add(p, fma(lap, inv_h2, -dd) - sg[q], false);
+      mag = fmax(mag, (fabs(lnb) + 6.0 * fabs(se[q])) * inv_h2 + fabs(dd) + fabs(sg[q]));
+    }
+    scale = block_max(mag);
+    p = block_reduce(p);
+    if (threadIdx.x == 0) {
+      const double mu = p.sum / (double)cells;
+      s_mu = mu;
+      s_res = (p.nonfinite > 0) ? NAN : fmax(p.dmax - mu, mu - p.dmin);
+    }
+    __syncthreads();
+    return s_res;
+  };
+  const double r0 = residual();
+  double r_prev = r0;
+  const int hn = n >> 1;
+  const int per_colour = hn * hn * n;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int colour = 0; colour < 4; ++colour) {
+      for (int t = threadIdx.x; t < per_colour; t += blockDim.x) {
+        const int m = t % hn, jj = (t / hn) % hn, k = t / (hn * hn);
+        const int i = 2 * m + ((colour ^ k) & 1);
+        const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
+        const int id = i + n * (j + n * k);
+        const StencilT<double> a = gather_periodic<double>(se, i, j, k, n);
+        const StencilT<double> b = gather_periodic<double>(sp, i, j, k, n);
+        se[id] = fma(-h2, ddv(a, b, sq[id]) + sg[id] + s_mu, a.sx + a.sy + a.sz) * (1.0 / 6.0);
+      }
+      __syncthreads();
+    }
+    if ((sweep & 1) == 1 || sweep + 1 == max_sweeps) {
+      const double r = residual();
+      if (coarsest_done(r, r0, r_prev, scale, drop)) break;
+      r_prev = r;
+    }
+  }
+  for (int q = threadIdx.x; q < cells; q += blockDim.x) e[q] = (float)se[q];
+  if (threadIdx.x == 0) {
+    sc->lambda = s_mu;
+    sc->res = s_res;
+  }
+}
+
+}  // namespace mg

@@ -38,6 +38,9 @@ struct OpConst64 {
   double c3;      // 4(1-w) alpha
   double k2s;     // sigma * k2, k2 = 2/c3
   double k2;
+  double e1h, c1h;  // 2*e1, 2*c1: the same terms written with A/2
+  double h2_6;      // h^2/6
+  double upd_s;     // -h^2 k2s / 6: the smoother's coefficient of sqrt(q)
   int mode;
 };
 
@@ -101,6 +104,19 @@ __device__ __forceinline__ StencilT<T> gather_periodic(const T* __restrict__ p, 
   return s;
 }
 
+// A/2 with A = (Sx-Sy)^2 + (Sx-Sz)^2 + (Sy-Sz)^2 = 2[a1(a1-a2) + a2^2], a1 = Sx-Sy,
+// a2 = Sx-Sz (the form is positive definite, so no cancellation).
+__device__ __forceinline__ double half_A(const StencilT<double>& s) {
+  const double a1 = s.sx - s.sy, a2 = s.sx - s.sz;
+  return fma(a1, a1 - a2, a2 * a2);
+}
+
+// sqrt(q) for q >= 0 as q * rsqrt(q) (rsqrt is within 1 ulp); 0 stays 0 and a NaN
+// stays NaN.
+__device__ __forceinline__ double sqrt_nonneg(double q) {
+  return (q == 0.0) ? 0.0 : q * rsqrt(q);
+}
+
 // D (the root of Eq. two_branch) from the stencil and the per-cell source term.
 // `guard` is set when the discriminant is negative.
 __device__ __forceinline__ double root_D(const StencilT<double>& s, double src,
@@ -109,16 +125,14 @@ __device__ __forceinline__ double root_D(const StencilT<double>& s, double src,
     guard = false;
     return src;
   }
-  const double a1 = s.sx - s.sy, a2 = s.sx - s.sz, a3 = s.sy - s.sz;
-  const double A = fma(a1, a1, fma(a2, a2, a3 * a3));
+  const double A2 = half_A(s);
   const double B = fma(s.cxy, s.cxy, fma(s.cxz, s.cxz, s.cyz * s.cyz));
   if (c.mode == OP_SQRT) {
-    const double q = fma(c.e1, A, fma(c.e2, B, src));
+    const double q = fma(c.e1h, A2, fma(c.e2, B, src));
     guard = q < 0.0;
-    const double r = sqrt(guard ? 0.0 : q);  // a NaN q stays NaN
-    return fma(c.k2s, r, -c.k2);
+    return fma(c.k2s, sqrt_nonneg(guard ? 0.0 : q), -c.k2);
   }
-  const double u = fma(c.c1, A, fma(c.c2, B, src));
+  const double u = fma(c.c1h, A2, fma(c.c2, B, src));
   const double q = fma(c.c3, u, 1.0);
   guard = q < 0.0;
   if (guard) return -c.k2;
@@ -190,6 +204,36 @@ __device__ __forceinline__ Partial block_reduce(Partial p) {
   }
   __syncthreads();
   return p;
+}
+
+// Maximum over the block; every thread returns it.
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double shm[32];
+  __shared__ double result;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if (lane == 0) shm[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    double w = lane < nw ? shm[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_down_sync(0xffffffffu, w, o));
+    if (lane == 0) result = w;
+  }
+  __syncthreads();
+  return result;
+}
+
+// Stopping rule of the one-CTA coarsest solves: the residual fell by `drop`, or
+// it reached the rounding level of the operator's terms (`scale` is the largest
+// term), or it stopped falling.
+__device__ __forceinline__ bool coarsest_done(double r, double r0, double r_prev, double scale,
+                                              double drop) {
+  if (!(r > drop * r0)) return true;
+  if (r <= 64.0 * 1.1102230246251565e-16 * scale) return true;
+  return r >= 0.95 * r_prev;
 }
 
 }  // namespace mg

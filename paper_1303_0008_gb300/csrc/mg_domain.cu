@@ -57,6 +57,7 @@ mg_status domain_create(Domain** out, int n, const mg_options& o) {
     set_error("host allocation");
     return MG_ENOMEM;
   }
+  init_subcycle();
   d->n = n;
   d->nlev = nl;
   d->lv.resize(nl);
@@ -139,9 +140,30 @@ struct Cycle64 {
   EventPairs* timer_a = nullptr;  // finest-level smoother launches of each half
   EventPairs* timer_b = nullptr;
 
+  // The sub-V-cycle from level l down, in one cluster launch.
+  void subcycle(int l) const {
+    SubCycleArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nlev = d->nlev - l;
+    for (int k = 0; k < a.nlev; ++k) {
+      Level& L = d->lv[l + k];
+      a.lv[k] = SubLevel64{L.n, L.phi, L.src, L.f, L.phihat, d->d_sc + l + k, ops[l + k]};
+    }
+    a.part = d->d_part;
+    a.nu_pre = o->nu_pre;
+    a.nu_post = o->nu_post;
+    a.coarse_sweeps = o->coarse_sweeps;
+    a.coarse_drop = o->coarse_drop;
+    launch_subcycle64(st, a);
+  }
+
   void descend(int l) const {
     Level& L = d->lv[l];
     LevelScalars* sc = d->d_sc + l;
+    if (o->fuse_coarse && l > 0 && L.n <= kSubcycleMaxN && d->nlev - l <= kSubcycleMaxLevels) {
+      subcycle(l);
+      return;
+    }
     if (l == d->nlev - 1) {
       launch_coarsest64(st, L.n, L.phi, L.src, L.f, ops[l], sc, o->coarse_sweeps, o->coarse_drop);
       return;

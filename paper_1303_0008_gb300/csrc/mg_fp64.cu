@@ -10,6 +10,7 @@
 // count over memory tiling.
 #include "mg_common.cuh"
 #include "mg_internal.h"
+#include "mg_bodies64.cuh"
 
 namespace mg {
 
@@ -24,24 +25,7 @@ __global__ void __launch_bounds__(256) k_smooth_colour64(int n, double* __restri
                                                          const double* __restrict__ f,
                                                          const LevelScalars* __restrict__ sc,
                                                          OpConst64 c, int colour) {
-  const int hn = n >> 1;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)hn * hn * n;
-  if (t >= total) return;
-  const int m = (int)(t % hn);
-  const long long rest = t / hn;
-  const int jj = (int)(rest % hn);
-  const int k = (int)(rest / hn);
-  const int i = 2 * m + ((colour ^ k) & 1);
-  const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
-  const long long id = lidx(i, j, k, n);
-  const StencilT<double> s = gather_periodic(phi, i, j, k, n);
-  bool g;
-  const double D = root_D(s, src[id], c, g);
-  double rhs = sc->lambda;
-  if (f) rhs += f[id];
-  const double lapnb = s.sx + s.sy + s.sz;
-  phi[id] = fma(-c.h2, D + rhs, lapnb) * (1.0 / 6.0);
+  b_smooth_colour64(n, phi, src, f, sc, c, colour, blockIdx.x);
 }
 
 // d = L^h phi - f with block partial norms.
@@ -73,61 +57,18 @@ __global__ void __launch_bounds__(256) k_residual64(int n, const double* __restr
 
 // Residual of the 8 children of each coarse cell, averaged (full weighting),
 // together with R phi; the partial norms cover every fine cell.
-__global__ void __launch_bounds__(128) k_residual_restrict64(
+__global__ void __launch_bounds__(256) k_residual_restrict64(
     int nf, const double* __restrict__ phi, const double* __restrict__ src,
     const double* __restrict__ f, OpConst64 c, double* __restrict__ phi_c,
     double* __restrict__ phihat_c, double* __restrict__ rd_c, Partial* __restrict__ partials) {
-  const int nc = nf >> 1;
-  const long long ccells = (long long)nc * nc * nc;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  Partial p;
-  partial_init(p);
-  if (t < ccells) {
-    const int I = (int)(t % nc);
-    const int J = (int)((t / nc) % nc);
-    const int K = (int)(t / ((long long)nc * nc));
-    double sphi = 0.0, sd = 0.0;
-#pragma unroll 1
-    for (int ch = 0; ch < 8; ++ch) {
-      const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
-      const long long id = lidx(i, j, k, nf);
-      const StencilT<double> s = gather_periodic(phi, i, j, k, nf);
-      bool g;
-      const double D = root_D(s, src[id], c, g);
-      const double ctr = phi[id];
-      const double lap = (s.sx + s.sy + s.sz) - 6.0 * ctr;
-      double d = fma(lap, c.inv_h2, -D);
-      if (f) d -= f[id];
-      partial_add(p, d, g);
-      sphi += ctr;
-      sd += d;
-    }
-    phi_c[t] = sphi * 0.125;
-    phihat_c[t] = sphi * 0.125;
-    rd_c[t] = sd * 0.125;
-  }
-  p = block_reduce(p);
-  if (threadIdx.x == 0) partials[blockIdx.x] = p;
+  b_residual_restrict64(nf, phi, src, f, c, phi_c, phihat_c, rd_c, partials, blockIdx.x);
 }
 
 // One block: reduce the partials in a fixed order and publish the scalars.
 __global__ void __launch_bounds__(256) k_finalize(const Partial* __restrict__ partials, int nparts,
                                                   double cells, int periodic,
                                                   LevelScalars* __restrict__ sc) {
-  Partial p;
-  partial_init(p);
-  for (int b = threadIdx.x; b < nparts; b += blockDim.x) partial_merge(p, partials[b]);
-  p = block_reduce(p);
-  if (threadIdx.x == 0) {
-    const double lam = periodic ? p.sum / cells : 0.0;
-    sc->lambda = lam;
-    sc->sum = p.sum;
-    sc->dmax = p.dmax;
-    sc->dmin = p.dmin;
-    sc->res = (p.nonfinite > 0) ? NAN : fmax(p.dmax - lam, lam - p.dmin);
-    sc->guards = p.guards;
-    sc->nonfinite = p.nonfinite;
-  }
+  b_finalize(partials, nparts, cells, periodic, sc, blockIdx.x);
 }
 
 // f^H = L^H(R phi) - (R d - lambda^h); lambda^H starts at 0.
@@ -136,19 +77,7 @@ __global__ void __launch_bounds__(256) k_fas_rhs64(int nc, const double* __restr
                                                    double* __restrict__ f_c, OpConst64 c,
                                                    const LevelScalars* __restrict__ fine_sc,
                                                    LevelScalars* __restrict__ coarse_sc) {
-  const long long cells = (long long)nc * nc * nc;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) coarse_sc->lambda = 0.0;
-  if (t >= cells) return;
-  const int i = (int)(t % nc);
-  const int j = (int)((t / nc) % nc);
-  const int k = (int)(t / ((long long)nc * nc));
-  const StencilT<double> s = gather_periodic(phi_c, i, j, k, nc);
-  bool g;
-  const double D = root_D(s, src_c[t], c, g);
-  const double lap = (s.sx + s.sy + s.sz) - 6.0 * phi_c[t];
-  const double L = fma(lap, c.inv_h2, -D);
-  f_c[t] = L - f_c[t] + fine_sc->lambda;
+  b_fas_rhs64(nc, phi_c, src_c, f_c, c, fine_sc, coarse_sc, blockIdx.x);
 }
 
 // phi^h += P(phi^H - R phi^h): cell-centred trilinear, per axis 3/4 on the parent
@@ -156,24 +85,7 @@ __global__ void __launch_bounds__(256) k_fas_rhs64(int nc, const double* __restr
 __global__ void __launch_bounds__(256) k_prolong_correct64(int nc, const double* __restrict__ phi_c,
                                                            const double* __restrict__ phihat_c,
                                                            double* __restrict__ phi_f) {
-  const int nf = nc << 1;
-  const long long cells = (long long)nf * nf * nf;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cells) return;
-  const int i = (int)(t % nf);
-  const int j = (int)((t / nf) % nf);
-  const int k = (int)(t / ((long long)nf * nf));
-  const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
-  const int I1 = (i & 1) ? wrap_up(I0, nc) : wrap_dn(I0, nc);
-  const int J1 = (j & 1) ? wrap_up(J0, nc) : wrap_dn(J0, nc);
-  const int K1 = (k & 1) ? wrap_up(K0, nc) : wrap_dn(K0, nc);
-  auto e = [&](int a, int b, int cc) {
-    const long long q = lidx(a, b, cc, nc);
-    return phi_c[q] - phihat_c[q];
-  };
-  const double v = 27.0 * e(I0, J0, K0) + 9.0 * (e(I1, J0, K0) + e(I0, J1, K0) + e(I0, J0, K1)) +
-                   3.0 * (e(I1, J1, K0) + e(I1, J0, K1) + e(I0, J1, K1)) + e(I1, J1, K1);
-  phi_f[t] += v * (1.0 / 64.0);
+  b_prolong_correct64(nc, phi_c, phihat_c, phi_f, blockIdx.x);
 }
 
 // Coarsest level in one CTA (n^3 <= 4096 cells in shared memory): four-colour
@@ -183,72 +95,7 @@ __global__ void __launch_bounds__(256) k_coarsest64(int n, double* __restrict__ 
                                                     const double* __restrict__ f, OpConst64 c,
                                                     LevelScalars* __restrict__ sc, int max_sweeps,
                                                     double drop, int check_every) {
-  extern __shared__ double smem64[];
-  __shared__ double s_lam, s_res0, s_res;
-  const int cells = n * n * n;
-  double* sphi = smem64;
-  double* ssrc = smem64 + cells;
-  double* sf = smem64 + 2 * cells;
-  for (int q = threadIdx.x; q < cells; q += blockDim.x) {
-    sphi[q] = phi[q];
-    ssrc[q] = src[q];
-    sf[q] = f ? f[q] : 0.0;
-  }
-  if (threadIdx.x == 0) s_lam = sc->lambda;
-  __syncthreads();
-  auto residual = [&](double& res_out) {
-    Partial p;
-    partial_init(p);
-    for (int q = threadIdx.x; q < cells; q += blockDim.x) {
-      const int i = q % n, j = (q / n) % n, k = q / (n * n);
-      const StencilT<double> s = gather_periodic<double>(sphi, i, j, k, n);
-      bool g;
-      const double D = root_D(s, ssrc[q], c, g);
-      const double lap = (s.sx + s.sy + s.sz) - 6.0 * sphi[q];
-      partial_add(p, fma(lap, c.inv_h2, -D) - sf[q], g);
-    }
-    p = block_reduce(p);
-    if (threadIdx.x == 0) {
-      const double lam = p.sum / (double)cells;
-      s_lam = lam;
-      s_res = (p.nonfinite > 0) ? NAN : fmax(p.dmax - lam, lam - p.dmin);
-      sc->guards = p.guards;
-      sc->nonfinite = p.nonfinite;
-    }
-    __syncthreads();
-    res_out = s_res;
-  };
-  double r;
-  residual(r);
-  if (threadIdx.x == 0) s_res0 = r;
-  __syncthreads();
-  const double r0 = s_res0;
-  const int hn = n >> 1;
-  const int per_colour = hn * hn * n;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    for (int colour = 0; colour < 4; ++colour) {
-      for (int t = threadIdx.x; t < per_colour; t += blockDim.x) {
-        const int m = t % hn, jj = (t / hn) % hn, k = t / (hn * hn);
-        const int i = 2 * m + ((colour ^ k) & 1);
-        const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
-        const int id = i + n * (j + n * k);
-        const StencilT<double> s = gather_periodic<double>(sphi, i, j, k, n);
-        bool g;
-        const double D = root_D(s, ssrc[id], c, g);
-        sphi[id] = fma(-c.h2, D + sf[id] + s_lam, s.sx + s.sy + s.sz) * (1.0 / 6.0);
-      }
-      __syncthreads();
-    }
-    if ((sweep + 1) % check_every == 0 || sweep + 1 == max_sweeps) {
-      residual(r);
-      if (!(r > drop * r0)) break;
-    }
-  }
-  for (int q = threadIdx.x; q < cells; q += blockDim.x) phi[q] = sphi[q];
-  if (threadIdx.x == 0) {
-    sc->lambda = s_lam;
-    sc->res = s_res;
-  }
+  b_coarsest64(n, phi, src, f, c, sc, max_sweeps, drop, check_every, blockIdx.x);
 }
 
 // coarse = mean of the 8 children.
@@ -276,41 +123,19 @@ __global__ void __launch_bounds__(256) k_affine64(long long cells, const double*
                                                   double* __restrict__ out, double a, double b,
                                                   double c3, int floor,
                                                   unsigned long long* __restrict__ floored) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  bool hit = false;
-  if (t < cells) {
-    double v = fma(a, delta[t], b);
-    if (floor) {
-      const double lhs = (b != 0.0) ? v : fma(c3, v, 1.0);  // 1 + c3 kappa delta
-      if (lhs < 0.0) {
-        hit = true;
-        v = (b != 0.0) ? 0.0 : -1.0 / c3;
-      }
-    }
-    out[t] = v;
-  }
-  if (floored) {
-    const unsigned ballot = __ballot_sync(0xffffffffu, hit);
-    if ((threadIdx.x & 31) == 0 && ballot) atomicAdd(floored, (unsigned long long)__popc(ballot));
-  }
+  b_affine64(cells, delta, out, a, b, c3, floor, floored, blockIdx.x);
 }
 
 // Partial sums of x (for the gauge fix).
 __global__ void __launch_bounds__(256) k_sum_partials(long long cells, const double* __restrict__ x,
                                                       Partial* __restrict__ partials) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  Partial p;
-  partial_init(p);
-  if (t < cells) partial_add(p, x[t], false);
-  p = block_reduce(p);
-  if (threadIdx.x == 0) partials[blockIdx.x] = p;
+  b_sum_partials(cells, x, partials, blockIdx.x);
 }
 
 // x -= mean (the mean sits in sc->lambda, computed by k_finalize).
 __global__ void __launch_bounds__(256) k_sub_mean(long long cells, double* __restrict__ x,
                                                   const LevelScalars* __restrict__ sc) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < cells) x[t] -= sc->lambda;
+  b_sub_mean(cells, x, sc, blockIdx.x);
 }
 
 // g = -(1/2) grad phi, central differences; out is 3 x n^3 (x, y, z).
@@ -341,6 +166,7 @@ OpConst64 make_op64(int n, double alpha, double kappa, int branch) {
   const double w = 1.0 / 3.0;
   c.h2 = h * h;
   c.inv_h2 = (double)n * (double)n;
+  c.h2_6 = c.h2 / 6.0;
   const double h4 = c.h2 * c.h2;
   c.c3 = 4.0 * (1.0 - w) * alpha;
   if (alpha == 0.0) {
@@ -354,6 +180,9 @@ OpConst64 make_op64(int n, double alpha, double kappa, int branch) {
   c.c2 = alpha / (8.0 * h4);
   c.e1 = c.c3 * c.c1;
   c.e2 = c.c3 * c.c2;
+  c.e1h = 2.0 * c.e1;
+  c.c1h = 2.0 * c.c1;
+  c.upd_s = -c.h2 * c.k2s / 6.0;
   // k2 (sigma sqrt(q) - 1) loses about |k2| * eps to cancellation on the physical
   // root; below |alpha| = 1e-4 the conjugate form 2u/(1+sqrt q) is used instead.
   c.mode = (sigma > 0 && fabs(alpha) < 1e-4) ? OP_CONJ : OP_SQRT;
@@ -401,8 +230,8 @@ void launch_residual_restrict64(cudaStream_t st, int nf, const double* phi, cons
                                 double* phihat_c, double* rd_c, Partial* partials,
                                 LevelScalars* sc) {
   const long long ccells = (long long)(nf / 2) * (nf / 2) * (nf / 2);
-  const unsigned nb = blocks_for(ccells, 128);
-  k_residual_restrict64<<<nb, 128, 0, st>>>(nf, phi, src, f, c, phi_c, phihat_c, rd_c, partials);
+  const unsigned nb = blocks_for(ccells, 256);
+  k_residual_restrict64<<<nb, 256, 0, st>>>(nf, phi, src, f, c, phi_c, phihat_c, rd_c, partials);
   k_finalize<<<1, 256, 0, st>>>(partials, (int)nb, (double)nf * nf * nf, 1, sc);
   count_launches(2);
 }

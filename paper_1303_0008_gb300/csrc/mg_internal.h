@@ -114,3 +114,40 @@ void launch_gauge64(cudaStream_t st, long long cells, double* x, Partial* partia
 void launch_force64(cudaStream_t st, int n, const double* phi, double* out);
 
 }  // namespace mg
+
+namespace mg {
+
+// Levels at or below this side run their whole sub-V-cycle in one launch of a
+// single thread-block cluster (see mg_subcycle.cu).
+constexpr int kSubcycleMaxN = 16;
+constexpr int kSubcycleMaxLevels = 8;
+
+struct SubLevel64 {
+  int n;
+  double *phi, *src, *f, *phihat;
+  LevelScalars* sc;
+  OpConst64 op;
+};
+
+struct SubLevel32 {
+  int n;
+  float *e, *ehat, *phi0, *q0, *rhs;
+  LevelScalars* sc32;
+  OpConst32 op32;
+};
+
+struct SubCycleArgs {
+  int nlev;  // levels handled, the entry level first
+  SubLevel64 lv[kSubcycleMaxLevels];
+  SubLevel32 lv32[kSubcycleMaxLevels];
+  Partial* part;
+  int nu_pre, nu_post, coarse_sweeps;
+  double coarse_drop;
+};
+
+// Enqueue the FP64 (or FP32-correction) sub-V-cycle described by `a` on `st`.
+void launch_subcycle64(cudaStream_t st, const SubCycleArgs& a);
+void launch_subcycle32(cudaStream_t st, const SubCycleArgs& a);
+void init_subcycle();
+
+}  // namespace mg

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "mg_internal.h"
+#include "mg_bodies32.cuh"
 #include "mg_solver.h"
 
 namespace mg {
@@ -34,35 +35,6 @@ namespace mg {
     }                                                                        \
   } while (0)
 
-// The change of the root D when phi0 moves by e, from the stencils of e and phi0.
-template <typename T>
-__device__ __forceinline__ T delta_D(const StencilT<T>& se, const StencilT<T>& sp, T q0, T g1,
-                                     T g2, T c3, T k2, T sigma, T& du_out) {
-  const T a1e = se.sx - se.sy, a2e = se.sx - se.sz, a3e = se.sy - se.sz;
-  const T a1p = sp.sx - sp.sy, a2p = sp.sx - sp.sz, a3p = sp.sy - sp.sz;
-  const T two = T(2);
-  const T dA = a1e * (two * a1p + a1e) + a2e * (two * a2p + a2e) + a3e * (two * a3p + a3e);
-  const T dB = se.cxy * (two * sp.cxy + se.cxy) + se.cxz * (two * sp.cxz + se.cxz) +
-               se.cyz * (two * sp.cyz + se.cyz);
-  const T du = g1 * dA + g2 * dB;
-  du_out = du;
-  const T q1 = q0 + c3 * du;
-  const T s0 = sqrt(q0 > T(0) ? q0 : T(0));
-  const T s1 = sqrt(q1 > T(0) ? q1 : T(0));
-  if (q0 >= T(0) && q1 >= T(0)) {
-    const T den = s0 + s1;
-    return den > T(0) ? sigma * two * du / den : T(0);
-  }
-  return sigma * k2 * (s1 - s0);
-}
-
-__device__ __forceinline__ float dD32(const StencilT<float>& se, const StencilT<float>& sp,
-                                      float q0, const OpConst32& c) {
-  if (c.linear) return 0.f;
-  float du;
-  return delta_D<float>(se, sp, q0, c.g1, c.g2, c.c3, c.k2, c.sigma, du);
-}
-
 // ---------------------------------------------------------------------------
 // FP64 outer residual with the FP32 hand-off.
 // ---------------------------------------------------------------------------
@@ -70,51 +42,13 @@ __global__ void __launch_bounds__(256) k_residual_handoff64(
     int n, const double* __restrict__ phi, const double* __restrict__ src, OpConst64 c,
     const LevelScalars* __restrict__ sc, float* __restrict__ g, float* __restrict__ q0,
     float* __restrict__ phi0, float* __restrict__ e, Partial* __restrict__ partials) {
-  const long long cells = (long long)n * n * n;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  Partial p;
-  partial_init(p);
-  if (t < cells) {
-    const int i = (int)(t % n);
-    const int j = (int)((t / n) % n);
-    const int k = (int)(t / ((long long)n * n));
-    const StencilT<double> s = gather_periodic(phi, i, j, k, n);
-    double q = 1.0, D;
-    bool guard = false;
-    if (c.mode == OP_LINEAR) {
-      D = src[t];
-    } else {
-      const double a1 = s.sx - s.sy, a2 = s.sx - s.sz, a3 = s.sy - s.sz;
-      const double A = fma(a1, a1, fma(a2, a2, a3 * a3));
-      const double B = fma(s.cxy, s.cxy, fma(s.cxz, s.cxz, s.cyz * s.cyz));
-      if (c.mode == OP_SQRT) {
-        q = fma(c.e1, A, fma(c.e2, B, src[t]));
-        D = fma(c.k2s, sqrt(q < 0.0 ? 0.0 : q), -c.k2);
-      } else {
-        const double u = fma(c.c1, A, fma(c.c2, B, src[t]));
-        q = fma(c.c3, u, 1.0);
-        D = (q < 0.0) ? -c.k2 : (2.0 * u) / (1.0 + sqrt(q));
-      }
-      guard = q < 0.0;
-    }
-    const double ctr = phi[t];
-    const double lap = (s.sx + s.sy + s.sz) - 6.0 * ctr;
-    const double d = fma(lap, c.inv_h2, -D);
-    partial_add(p, d, guard);
-    g[t] = (float)(sc->lambda - d);
-    q0[t] = (float)q;
-    phi0[t] = (float)ctr;
-    e[t] = 0.f;
-  }
-  p = block_reduce(p);
-  if (threadIdx.x == 0) partials[blockIdx.x] = p;
+  b_residual_handoff64(n, phi, src, c, sc, g, q0, phi0, e, partials, blockIdx.x);
 }
 
 // phi += e (FP64).
 __global__ void __launch_bounds__(256) k_update64(long long cells, double* __restrict__ phi,
                                                   const float* __restrict__ e) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < cells) phi[t] += (double)e[t];
+  b_update64(cells, phi, e, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -122,18 +56,7 @@ __global__ void __launch_bounds__(256) k_update64(long long cells, double* __res
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_restrict32(int nc, const float* __restrict__ fine,
                                                     float* __restrict__ coarse) {
-  const int nf = nc << 1;
-  const long long cells = (long long)nc * nc * nc;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cells) return;
-  const int I = (int)(t % nc);
-  const int J = (int)((t / nc) % nc);
-  const int K = (int)(t / ((long long)nc * nc));
-  float s = 0.f;
-#pragma unroll
-  for (int ch = 0; ch < 8; ++ch)
-    s += fine[lidx(2 * I + (ch & 1), 2 * J + ((ch >> 1) & 1), 2 * K + (ch >> 2), nf)];
-  coarse[t] = s * 0.125f;
+  b_restrict32(nc, fine, coarse, blockIdx.x);
 }
 
 // q0 = 1 + 4(1-w) alpha (kappa delta + alpha Sigma_d(phi0)) on a coarse level; with
@@ -142,23 +65,7 @@ __global__ void __launch_bounds__(256) k_q0_prep32(int n, const float* __restric
                                                    const double* __restrict__ delta,
                                                    OpConst32 c, float kappa, int floor,
                                                    float* __restrict__ q0) {
-  const long long cells = (long long)n * n * n;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cells) return;
-  if (c.linear) {
-    q0[t] = 1.f;
-    return;
-  }
-  const int i = (int)(t % n);
-  const int j = (int)((t / n) % n);
-  const int k = (int)(t / ((long long)n * n));
-  const StencilT<float> s = gather_periodic(phi0, i, j, k, n);
-  const float a1 = s.sx - s.sy, a2 = s.sx - s.sz, a3 = s.sy - s.sz;
-  const float A = a1 * a1 + a2 * a2 + a3 * a3;
-  const float B = s.cxy * s.cxy + s.cxz * s.cxz + s.cyz * s.cyz;
-  float qs = fmaf(c.c3 * kappa, (float)delta[t], 1.f);
-  if (floor && qs < 0.f) qs = 0.f;
-  q0[t] = fmaf(c.c3, c.g1 * A + c.g2 * B, qs);
+  b_q0_prep32(n, phi0, delta, c, kappa, floor, q0, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_smooth_colour32(int n, float* __restrict__ e,
@@ -167,66 +74,16 @@ __global__ void __launch_bounds__(256) k_smooth_colour32(int n, float* __restric
                                                          const float* __restrict__ g,
                                                          const LevelScalars* __restrict__ sc,
                                                          OpConst32 c, int colour) {
-  const int hn = n >> 1;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)hn * hn * n;
-  if (t >= total) return;
-  const int m = (int)(t % hn);
-  const long long rest = t / hn;
-  const int jj = (int)(rest % hn);
-  const int k = (int)(rest / hn);
-  const int i = 2 * m + ((colour ^ k) & 1);
-  const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
-  const long long id = lidx(i, j, k, n);
-  const StencilT<float> se = gather_periodic(e, i, j, k, n);
-  float dd = 0.f;
-  if (!c.linear) {
-    const StencilT<float> sp = gather_periodic(phi0, i, j, k, n);
-    dd = dD32(se, sp, q0[id], c);
-  }
-  const float rhs = g[id] + (float)sc->lambda;
-  e[id] = fmaf(-c.h2, dd + rhs, se.sx + se.sy + se.sz) * (1.f / 6.f);
+  b_smooth_colour32(n, e, phi0, q0, g, sc, c, colour, blockIdx.x);
 }
 
 // rho = N(e) - g on the 8 children of each coarse cell; R e and R rho.
-__global__ void __launch_bounds__(128) k_residual_restrict32(
+__global__ void __launch_bounds__(256) k_residual_restrict32(
     int nf, const float* __restrict__ e, const float* __restrict__ phi0,
     const float* __restrict__ q0, const float* __restrict__ g, OpConst32 c,
     float* __restrict__ e_c, float* __restrict__ ehat_c, float* __restrict__ rg_c,
     Partial* __restrict__ partials) {
-  const int nc = nf >> 1;
-  const long long ccells = (long long)nc * nc * nc;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  Partial p;
-  partial_init(p);
-  if (t < ccells) {
-    const int I = (int)(t % nc);
-    const int J = (int)((t / nc) % nc);
-    const int K = (int)(t / ((long long)nc * nc));
-    float se_sum = 0.f, sr = 0.f;
-#pragma unroll 1
-    for (int ch = 0; ch < 8; ++ch) {
-      const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
-      const long long id = lidx(i, j, k, nf);
-      const StencilT<float> se = gather_periodic(e, i, j, k, nf);
-      float dd = 0.f;
-      if (!c.linear) {
-        const StencilT<float> sp = gather_periodic(phi0, i, j, k, nf);
-        dd = dD32(se, sp, q0[id], c);
-      }
-      const float ctr = e[id];
-      const float lap = (se.sx + se.sy + se.sz) - 6.f * ctr;
-      const float r = fmaf(lap, c.inv_h2, -dd) - g[id];
-      partial_add(p, (double)r, false);
-      se_sum += ctr;
-      sr += r;
-    }
-    e_c[t] = se_sum * 0.125f;
-    ehat_c[t] = se_sum * 0.125f;
-    rg_c[t] = sr * 0.125f;
-  }
-  p = block_reduce(p);
-  if (threadIdx.x == 0) partials[blockIdx.x] = p;
+  b_residual_restrict32(nf, e, phi0, q0, g, c, e_c, ehat_c, rg_c, partials, blockIdx.x);
 }
 
 // g^H = N^H(R e) - (R rho - mu^h); mu^H starts at 0.
@@ -236,45 +93,13 @@ __global__ void __launch_bounds__(256) k_fas_rhs32(int nc, const float* __restri
                                                    float* __restrict__ g_c, OpConst32 c,
                                                    const LevelScalars* __restrict__ fine_sc,
                                                    LevelScalars* __restrict__ coarse_sc) {
-  const long long cells = (long long)nc * nc * nc;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) coarse_sc->lambda = 0.0;
-  if (t >= cells) return;
-  const int i = (int)(t % nc);
-  const int j = (int)((t / nc) % nc);
-  const int k = (int)(t / ((long long)nc * nc));
-  const StencilT<float> se = gather_periodic(e_c, i, j, k, nc);
-  float dd = 0.f;
-  if (!c.linear) {
-    const StencilT<float> sp = gather_periodic(phi0_c, i, j, k, nc);
-    dd = dD32(se, sp, q0_c[t], c);
-  }
-  const float lap = (se.sx + se.sy + se.sz) - 6.f * e_c[t];
-  const float Nv = fmaf(lap, c.inv_h2, -dd);
-  g_c[t] = Nv - g_c[t] + (float)fine_sc->lambda;
+  b_fas_rhs32(nc, e_c, phi0_c, q0_c, g_c, c, fine_sc, coarse_sc, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_prolong_correct32(int nc, const float* __restrict__ e_c,
                                                            const float* __restrict__ ehat_c,
                                                            float* __restrict__ e_f) {
-  const int nf = nc << 1;
-  const long long cells = (long long)nf * nf * nf;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cells) return;
-  const int i = (int)(t % nf);
-  const int j = (int)((t / nf) % nf);
-  const int k = (int)(t / ((long long)nf * nf));
-  const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
-  const int I1 = (i & 1) ? wrap_up(I0, nc) : wrap_dn(I0, nc);
-  const int J1 = (j & 1) ? wrap_up(J0, nc) : wrap_dn(J0, nc);
-  const int K1 = (k & 1) ? wrap_up(K0, nc) : wrap_dn(K0, nc);
-  auto v = [&](int a, int b, int cc) {
-    const long long q = lidx(a, b, cc, nc);
-    return e_c[q] - ehat_c[q];
-  };
-  const float s = 27.f * v(I0, J0, K0) + 9.f * (v(I1, J0, K0) + v(I0, J1, K0) + v(I0, J0, K1)) +
-                  3.f * (v(I1, J1, K0) + v(I1, J0, K1) + v(I0, J1, K1)) + v(I1, J1, K1);
-  e_f[t] += s * (1.f / 64.f);
+  b_prolong_correct32(nc, e_c, ehat_c, e_f, blockIdx.x);
 }
 
 // Coarsest inner level in one CTA, in FP64: sweeps of N(e) = g + mu until the
@@ -285,74 +110,7 @@ __global__ void __launch_bounds__(256) k_coarsest_corr64(int n, float* __restric
                                                          const float* __restrict__ g, OpConst32 c,
                                                          LevelScalars* __restrict__ sc,
                                                          int max_sweeps, double drop) {
-  extern __shared__ double smc[];
-  __shared__ double s_mu, s_res0, s_res;
-  const int cells = n * n * n;
-  double* se = smc;
-  double* sp = smc + cells;
-  double* sq = smc + 2 * cells;
-  double* sg = smc + 3 * cells;
-  for (int q = threadIdx.x; q < cells; q += blockDim.x) {
-    se[q] = e[q];
-    sp[q] = phi0[q];
-    sq[q] = q0[q];
-    sg[q] = g[q];
-  }
-  if (threadIdx.x == 0) s_mu = sc->lambda;
-  __syncthreads();
-  const double h2 = (double)c.h2, inv_h2 = (double)c.inv_h2;
-  const double g1 = (double)c.g1, g2 = (double)c.g2, c3 = (double)c.c3, k2 = (double)c.k2,
-               sigma = (double)c.sigma;
-  auto ddv = [&](const StencilT<double>& a, const StencilT<double>& b, double qq) {
-    if (c.linear) return 0.0;
-    double du;
-    return delta_D<double>(a, b, qq, g1, g2, c3, k2, sigma, du);
-  };
-  auto residual = [&]() {
-    Partial p;
-    partial_init(p);
-    for (int q = threadIdx.x; q < cells; q += blockDim.x) {
-      const int i = q % n, j = (q / n) % n, k = q / (n * n);
-      const StencilT<double> a = gather_periodic<double>(se, i, j, k, n);
-      const StencilT<double> b = gather_periodic<double>(sp, i, j, k, n);
-      const double lap = (a.sx + a.sy + a.sz) - 6.0 * se[q];
-      partial_add(p, fma(lap, inv_h2, -ddv(a, b, sq[q])) - sg[q], false);
-    }
-    p = block_reduce(p);
-    if (threadIdx.x == 0) {
-      const double mu = p.sum / (double)cells;
-      s_mu = mu;
-      s_res = (p.nonfinite > 0) ? NAN : fmax(p.dmax - mu, mu - p.dmin);
-    }
-    __syncthreads();
-    return s_res;
-  };
-  const double r0 = residual();
-  const int hn = n >> 1;
-  const int per_colour = hn * hn * n;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    for (int colour = 0; colour < 4; ++colour) {
-      for (int t = threadIdx.x; t < per_colour; t += blockDim.x) {
-        const int m = t % hn, jj = (t / hn) % hn, k = t / (hn * hn);
-        const int i = 2 * m + ((colour ^ k) & 1);
-        const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
-        const int id = i + n * (j + n * k);
-        const StencilT<double> a = gather_periodic<double>(se, i, j, k, n);
-        const StencilT<double> b = gather_periodic<double>(sp, i, j, k, n);
-        se[id] = fma(-h2, ddv(a, b, sq[id]) + sg[id] + s_mu, a.sx + a.sy + a.sz) * (1.0 / 6.0);
-      }
-      __syncthreads();
-    }
-    if ((sweep & 1) == 1 || sweep + 1 == max_sweeps) {
-      const double r = residual();
-      if (!(r > drop * r0)) break;
-    }
-  }
-  for (int q = threadIdx.x; q < cells; q += blockDim.x) e[q] = (float)se[q];
-  if (threadIdx.x == 0) {
-    sc->lambda = s_mu;
-    sc->res = s_res;
-  }
+  b_coarsest_corr64(n, e, phi0, q0, g, c, sc, max_sweeps, drop, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -422,6 +180,8 @@ static mg_status mixed_prepare(Domain* d) {
   return MG_OK;
 }
 
+mg_status mixed_prepare_domain(Domain* d) { return mixed_prepare(d); }
+
 struct CycleMixed {
   Domain* d;
   const mg_options* o;
@@ -443,8 +203,28 @@ struct CycleMixed {
     count_launches(4LL * sweeps);
   }
 
+  void subcycle(int l) const {
+    SubCycleArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nlev = d->nlev - l;
+    for (int k = 0; k < a.nlev; ++k) {
+      Level& L = d->lv[l + k];
+      a.lv32[k] = SubLevel32{L.n, L.e, L.ehat, L.phi0, L.q0, L.rhs, sc32(l + k), ops32[l + k]};
+    }
+    a.part = d->d_part;
+    a.nu_pre = o->nu_pre;
+    a.nu_post = o->nu_post;
+    a.coarse_sweeps = o->coarse_sweeps;
+    a.coarse_drop = o->coarse_drop;
+    launch_subcycle32(st, a);
+  }
+
   void inner(int l) const {
     Level& L = d->lv[l];
+    if (o->fuse_coarse && l > 0 && L.n <= kSubcycleMaxN && d->nlev - l <= kSubcycleMaxLevels) {
+      subcycle(l);
+      return;
+    }
     if (l == d->nlev - 1) {
       const size_t smem = 4 * sizeof(double) * (size_t)L.cells;
       k_coarsest_corr64<<<1, 256, smem, st>>>(L.n, L.e, L.phi0, L.q0, L.rhs, ops32[l], sc32(l),
@@ -454,8 +234,8 @@ struct CycleMixed {
     }
     Level& C = d->lv[l + 1];
     smooth(l, o->nu_pre);
-    const unsigned nb = nblk(C.cells, 128);
-    k_residual_restrict32<<<nb, 128, 0, st>>>(L.n, L.e, L.phi0, L.q0, L.rhs, ops32[l], C.e,
+    const unsigned nb = nblk(C.cells, 256);
+    k_residual_restrict32<<<nb, 256, 0, st>>>(L.n, L.e, L.phi0, L.q0, L.rhs, ops32[l], C.e,
                                                C.ehat, C.rhs, d->d_part);
     launch_finalize(st, d->d_part, (int)nb, (double)L.cells, 1, sc32(l));
     k_fas_rhs32<<<nblk(C.cells, 256), 256, 0, st>>>(C.n, C.e, C.phi0, C.q0, C.rhs, ops32[l + 1],

@@ -35,7 +35,7 @@ class mg_options(ctypes.Structure):
                 ("inner_cycles", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("coarse_sweeps", ctypes.c_int), ("coarse_drop", ctypes.c_double),
                 ("time_kernels", ctypes.c_int), ("guard", ctypes.c_int),
-                ("patch_coarse_sweeps", ctypes.c_int)]
+                ("patch_coarse_sweeps", ctypes.c_int), ("fuse_coarse", ctypes.c_int)]
 
 
 class mg_solve_stats(ctypes.Structure):

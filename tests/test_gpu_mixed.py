@@ -109,3 +109,11 @@ def test_mixed_full_size_128_against_fp64_and_oracle_residual():
         mg.mg_destroy_grid(g)
     assert rel(phi_m, phi_64) < 1e-7
     assert rel(force_m, O.force(phi_64)) < 1e-7
+
+
+def test_mixed_fused_coarse_subcycle_is_bit_identical():
+    delta = I.lognormal_delta(64, 1.5, 8)
+    a, _, s1 = solve(delta, 0.3, 1.0, tol=1e-10, fuse_coarse=1)
+    b, _, s2 = solve(delta, 0.3, 1.0, tol=1e-10, fuse_coarse=0)
+    assert s1["rc"] == s2["rc"] == mg.MG_OK
+    assert np.array_equal(a, b) and s1["hist"] == s2["hist"]

@@ -296,6 +296,18 @@ def test_host_buffers_and_determinism():
     assert s1["hist"] == s2["hist"] == s3["hist"]
 
 
+@pytest.mark.parametrize("n", [32, 48, 64])
+def test_fused_coarse_subcycle_is_bit_identical(n):
+    """The levels with <= 16 cells per side run as one cluster launch that calls the
+    per-level kernels' bodies with the same block partition: the same bits."""
+    delta = I.lognormal_delta(n, 1.5, 7)
+    a, _, s1 = gpu_solve(delta, 0.3, 1.0, tol=1e-10, fuse_coarse=1)
+    b, _, s2 = gpu_solve(delta, 0.3, 1.0, tol=1e-10, fuse_coarse=0)
+    assert s1["rc"] == s2["rc"] == mg.MG_OK
+    assert np.array_equal(a, b) and s1["hist"] == s2["hist"]
+    assert s1["launches"] < s2["launches"]
+
+
 def test_errors_are_reported():
     n = 16
     with pytest.raises(mg.MGError) as e:
