@@ -139,7 +139,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("mg_fp64.cu", "mg_common.cuh"):
+    for f in ("mg_fp64.cu", "mg_bodies64.cuh", "mg_common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1303_0008_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -98,6 +98,13 @@ typedef struct {
                               refinement union per V-cycle (default 8) */
   int fuse_coarse;   /* 1: run the levels with <= 16 cells per side, down to the
                         coarsest, as one launch of a thread-block cluster (default 1) */
+  double omega;      /* relaxation of the FP64 Newton step on the periodic grid:
+                        phi += omega (phi_newton - phi); default 1 (the plain step) */
+  double omega_patch;/* the same on refinement levels (default 1) */
+  int patch_mg_levels;/* multigrid levels of a refinement union: 1 (smoothing only),
+                        2 (8^3 and 4^3 per patch) or 3 (down to 2^3; default) */
+  double patch_cgc;  /* scale of the coarse-grid correction on refinement unions
+                        (1 = the full FAS correction; default 1) */
 } mg_options;
 
 typedef struct {
@@ -123,7 +130,7 @@ typedef struct {
 void mg_default_options(mg_options* opt);
 
 /*
- * Create a periodic n^3 domain grid (n even, 4 <= n <= 2048).  `opt` may be NULL
+ * Create a periodic n^3 domain grid (n even, 4 <= n <= 1024).  `opt` may be NULL
  * (defaults).  Allocates the level hierarchy n, n/2, ... down to `coarsest`
  * (halving while the half is even and at least 4) on the current device.
  * Errors: MG_EINVAL for a bad n or options, MG_ENOMEM, MG_ECUDA.
@@ -182,6 +189,33 @@ mg_status mg_get_field(const mg_grid* g, int level, int patch, double* out, int 
  * differences at patch faces use the neighbouring patch or the Dirichlet fill.
  */
 mg_status mg_get_force(const mg_grid* g, int level, int patch, double* out, int on_device);
+
+/* Read or replace the options of a handle (the level hierarchy and the grid
+ * size stay as created; `coarsest` is not changed by mg_set_options). */
+mg_status mg_get_options(const mg_grid* g, mg_options* out);
+mg_status mg_set_options(mg_grid* g, const mg_options* opt);
+
+/*
+ * Autotuner.  Solves the handle's problem (its density and the field the caller
+ * left in it, restored before every trial) with every combination of
+ * nu_pre, nu_post in {1,2,3}, fuse_coarse in {0,1} and, for MG_MIXED,
+ * inner_cycles in {1,2,3,4}; each candidate is solved twice and timed on the
+ * device (the second solve counts).  The fastest candidate that converges to
+ * `tol` becomes the handle's options and is returned in *best (may be NULL) with
+ * its time in *best_seconds (may be NULL).  With a cache_path, the choice is
+ * stored in that JSON file under the key "n=<n>,prec=<fp64|mixed>,device=<name>";
+ * with use_cache = 1 a stored choice is applied without any trial.
+ * The field left in the handle is the caller's, unchanged.
+ * Errors: MG_EINVAL, MG_ESTATE (no density), MG_ENOCONV (no candidate converged),
+ * MG_ENOMEM, MG_ECUDA.
+ */
+mg_status mg_autotune(mg_grid* g, int branch, double alpha, double kappa, double tol,
+                      const char* cache_path, int use_cache, mg_options* best,
+                      double* best_seconds);
+
+/* Statistics of the last solve of a refinement level (level >= 1): cycles,
+ * status, final residual and the residual after each cycle. */
+mg_status mg_get_level_stats(const mg_grid* g, int level, mg_solve_stats* out);
 
 /* Release the handle and all of its device memory.  NULL is ignored. */
 void mg_destroy_grid(mg_grid* g);

@@ -58,6 +58,10 @@ void mg_default_options(mg_options* opt) {
   opt->guard = MG_GUARD_FLOOR;
   opt->patch_coarse_sweeps = 8;
   opt->fuse_coarse = 1;
+  opt->omega = 1.0;
+  opt->omega_patch = 1.0;
+  opt->patch_mg_levels = 3;
+  opt->patch_cgc = 1.0;
 }
 
 static mg_status check_options(const mg_options& o) {
@@ -74,6 +78,10 @@ static mg_status check_options(const mg_options& o) {
   if (o.patch_coarse_sweeps < 1 || o.patch_coarse_sweeps > 10000)
     MG_FAIL(MG_EINVAL, "options: patch_coarse_sweeps");
   if (o.fuse_coarse != 0 && o.fuse_coarse != 1) MG_FAIL(MG_EINVAL, "options: fuse_coarse");
+  if (!(o.omega > 0.0 && o.omega <= 1.0) || !(o.omega_patch > 0.0 && o.omega_patch <= 1.0))
+    MG_FAIL(MG_EINVAL, "options: omega and omega_patch must be in (0, 1]");
+  if (o.patch_mg_levels < 1 || o.patch_mg_levels > 3) MG_FAIL(MG_EINVAL, "options: patch_mg_levels");
+  if (!(o.patch_cgc > 0.0 && o.patch_cgc <= 1.0)) MG_FAIL(MG_EINVAL, "options: patch_cgc");
   return MG_OK;
 }
 
@@ -152,6 +160,39 @@ void mg_destroy_grid(mg_grid* g) {
   if (g->force_tmp) cudaFree(g->force_tmp);
   if (g->own_stream) cudaStreamDestroy(g->own_stream);
   delete g;
+}
+
+mg_status mg_get_level_stats(const mg_grid* g, int level, mg_solve_stats* out) {
+  if (!g || !out || g->batch) MG_FAIL(MG_EINVAL, "mg_get_level_stats: arguments");
+  if (level < 1 || level > (int)g->patch_levels.size() || !g->patch_levels[level - 1])
+    MG_FAIL(MG_EINVAL, "mg_get_level_stats: no patches on that level");
+  const PatchLevel* pl = g->patch_levels[level - 1];
+  std::memset(out, 0, sizeof(*out));
+  out->cycles = pl->last_cycles;
+  out->status = pl->last_status;
+  out->levels = 3;
+  out->res = pl->last_res;
+  out->res0 = pl->last_hist.empty() ? 0.0 : pl->last_hist.front();
+  for (double r : pl->last_hist)
+    if (out->hist_len < 128) out->res_hist[out->hist_len++] = r;
+  return MG_OK;
+}
+
+mg_status mg_get_options(const mg_grid* g, mg_options* out) {
+  if (!g || !out) MG_FAIL(MG_EINVAL, "mg_get_options: NULL argument");
+  *out = g->opt;
+  return MG_OK;
+}
+
+mg_status mg_set_options(mg_grid* g, const mg_options* opt) {
+  if (!g || !opt) MG_FAIL(MG_EINVAL, "mg_set_options: NULL argument");
+  mg_options o = *opt;
+  o.coarsest = g->opt.coarsest;
+  mg_status st = check_options(o);
+  if (st != MG_OK) return st;
+  g->opt = o;
+  for (Domain* d : g->domains) domain_invalidate_graphs(d);
+  return MG_OK;
 }
 
 mg_status mg_set_stream(mg_grid* g, void* stream) {
@@ -340,7 +381,7 @@ mg_status mg_solve_batch(mg_grid* g, const int* branch, const double* alpha, con
 // Single-kernel entry points
 // ---------------------------------------------------------------------------
 static mg_status check_n(int n) {
-  if (n < 4 || (n & 1) || n > 2048) MG_FAIL(MG_EINVAL, "n must be even and in [4, 2048]");
+  if (n < 4 || (n & 1) || n > 1024) MG_FAIL(MG_EINVAL, "n must be even and in [4, 1024]");
   return MG_OK;
 }
 

@@ -1,0 +1,194 @@
+// Autotuner: pick the sweep counts (and, for the mixed path, the inner V-cycles
+// per FP64 correction) that give the shortest time to the requested residual on
+// the handle's own problem, and remember the choice in a small JSON file keyed by
+// grid size, precision and device name.
+//
+// Each trial restores the field the caller left in the handle, solves with one
+// candidate, and reads the device time of the solve (CUDA events).  Candidates
+// that do not converge are discarded.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/mg.h"
+#include "mg_internal.h"
+#include "mg_solver.h"
+
+namespace mg {
+
+static std::string cache_key(int n, int prec) {
+  cudaDeviceProp p;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::string name = "unknown";
+  if (cudaGetDeviceProperties(&p, dev) == cudaSuccess) name = p.name;
+  for (char& c : name)
+    if (c == '"' || c == '\\') c = '_';
+  return "n=" + std::to_string(n) + ",prec=" + (prec == MG_MIXED ? "mixed" : "fp64") +
+         ",device=" + name;
+}
+
+// The cache is one JSON object: {"<key>": {"nu_pre": a, "nu_post": b,
+// "inner_cycles": c, "fuse_coarse": d, "seconds": t}, ...}.  This reader accepts
+// exactly the layout the writer below produces.
+static std::map<std::string, std::map<std::string, double>> read_cache(const std::string& path) {
+  std::map<std::string, std::map<std::string, double>> out;
+  std::ifstream f(path);
+  if (!f) return out;
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string s = ss.str();
+  size_t i = 0;
+  auto next_string = [&](std::string& v) -> bool {
+    const size_t a = s.find('"', i);
+    if (a == std::string::npos) return false;
+    const size_t b = s.find('"', a + 1);
+    if (b == std::string::npos) return false;
+    v = s.substr(a + 1, b - a - 1);
+    i = b + 1;
+    return true;
+  };
+  while (true) {
+    std::string key;
+    if (!next_string(key)) break;
+    const size_t open = s.find('{', i), close = s.find('}', i);
+    if (open == std::string::npos || close == std::string::npos || close < open) break;
+    i = open + 1;
+    std::map<std::string, double> fields;
+    while (true) {
+      const size_t q = s.find('"', i);
+      if (q == std::string::npos || q > close) break;
+      std::string name;
+      if (!next_string(name)) break;
+      const size_t colon = s.find(':', i);
+      if (colon == std::string::npos || colon > close) break;
+      fields[name] = std::strtod(s.c_str() + colon + 1, nullptr);
+      i = colon + 1;
+    }
+    out[key] = fields;
+    i = close + 1;
+  }
+  return out;
+}
+
+static bool write_cache(const std::string& path,
+                        const std::map<std::string, std::map<std::string, double>>& c) {
+  std::ofstream f(path, std::ios::trunc);
+  if (!f) return false;
+  f << "{\n";
+  size_t k = 0;
+  for (const auto& e : c) {
+    f << "  \"" << e.first << "\": {";
+    size_t j = 0;
+    for (const auto& v : e.second) {
+      char buf[64];
+      std::snprintf(buf, sizeof(buf), "%.9g", v.second);
+      f << "\"" << v.first << "\": " << buf << (++j < e.second.size() ? ", " : "");
+    }
+    f << "}" << (++k < c.size() ? "," : "") << "\n";
+  }
+  f << "}\n";
+  return (bool)f;
+}
+
+}  // namespace mg
+
+using namespace mg;
+
+extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double kappa, double tol,
+                                 const char* cache_path, int use_cache, mg_options* best,
+                                 double* best_seconds) {
+  if (!g || g->batch) {
+    set_error("mg_autotune: needs a domain handle");
+    return MG_EINVAL;
+  }
+  Domain* d = g->domains[0];
+  if (!d->density_set) {
+    set_error("mg_autotune: density not set");
+    return MG_ESTATE;
+  }
+  const std::string key = cache_key(d->n, g->opt.prec);
+  std::map<std::string, std::map<std::string, double>> cache;
+  if (cache_path && *cache_path) cache = read_cache(cache_path);
+  if (use_cache && cache.count(key)) {
+    const auto& e = cache[key];
+    mg_options o = g->opt;
+    o.nu_pre = (int)e.at("nu_pre");
+    o.nu_post = (int)e.at("nu_post");
+    o.inner_cycles = (int)e.at("inner_cycles");
+    o.fuse_coarse = (int)e.at("fuse_coarse");
+    g->opt = o;
+    if (best) *best = o;
+    if (best_seconds) *best_seconds = e.count("seconds") ? e.at("seconds") : -1.0;
+    return MG_OK;
+  }
+  // keep the caller's field to restart every trial from it
+  double* saved = nullptr;
+  const size_t bytes = sizeof(double) * (size_t)d->lv[0].cells;
+  if (cudaMalloc(&saved, bytes) != cudaSuccess) {
+    set_error("mg_autotune: device allocation");
+    return MG_ENOMEM;
+  }
+  cudaMemcpyAsync(saved, d->lv[0].phi, bytes, cudaMemcpyDeviceToDevice, g->stream);
+  const mg_options base = g->opt;
+  std::vector<mg_options> cands;
+  const int inner_set[] = {1, 2, 3, 4};
+  for (int pre = 1; pre <= 3; ++pre)
+    for (int post = 1; post <= 3; ++post)
+      for (int ic = 0; ic < (base.prec == MG_MIXED ? 4 : 1); ++ic)
+        for (int fuse = 0; fuse <= 1; ++fuse) {
+          mg_options o = base;
+          o.nu_pre = pre;
+          o.nu_post = post;
+          o.inner_cycles = base.prec == MG_MIXED ? inner_set[ic] : base.inner_cycles;
+          o.fuse_coarse = fuse;
+          cands.push_back(o);
+        }
+  double t_best = 1e300;
+  mg_options o_best = base;
+  mg_status result = MG_ENOCONV;
+  for (const mg_options& o : cands) {
+    double t = 0.0;
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {  // the first solve also captures graphs
+      cudaMemcpyAsync(d->lv[0].phi, saved, bytes, cudaMemcpyDeviceToDevice, g->stream);
+      mg_solve_stats st;
+      const mg_status s = domain_solve(d, o, g->stream, branch, alpha, kappa, tol, &st);
+      ok = (s == MG_OK);
+      t = st.wall_s;
+    }
+    if (ok && t < t_best) {
+      t_best = t;
+      o_best = o;
+      result = MG_OK;
+    }
+  }
+  cudaMemcpyAsync(d->lv[0].phi, saved, bytes, cudaMemcpyDeviceToDevice, g->stream);
+  cudaStreamSynchronize(g->stream);
+  cudaFree(saved);
+  if (result != MG_OK) {
+    set_error("mg_autotune: no candidate converged");
+    return result;
+  }
+  g->opt = o_best;
+  if (best) *best = o_best;
+  if (best_seconds) *best_seconds = t_best;
+  if (cache_path && *cache_path) {
+    cache[key] = {{"nu_pre", (double)o_best.nu_pre},
+                  {"nu_post", (double)o_best.nu_post},
+                  {"inner_cycles", (double)o_best.inner_cycles},
+                  {"fuse_coarse", (double)o_best.fuse_coarse},
+                  {"seconds", t_best}};
+    if (!write_cache(cache_path, cache)) {
+      set_error("mg_autotune: cannot write the cache file");
+      return MG_EINVAL;
+    }
+  }
+  return MG_OK;
+}

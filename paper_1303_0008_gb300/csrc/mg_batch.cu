@@ -458,7 +458,8 @@ mg_status mixed_prepare_domain(Domain* d);
 void launch_gauge64(cudaStream_t st, long long cells, double* x, Partial* partials,
                     LevelScalars* sc);
 mg_status domain_prepare_sources(Domain* d, cudaStream_t st, int branch, double alpha,
-                                 double kappa, int guard, std::vector<OpConst64>& ops);
+                                 double kappa, int guard, double omega,
+                                 std::vector<OpConst64>& ops);
 OpConst32 make_op32(int n, double alpha, int branch);
 
 mg_status batch_solve(mg_grid* g, const int* branch, const double* alpha, const double* kappa,
@@ -496,7 +497,8 @@ mg_status batch_solve(mg_grid* g, const int* branch, const double* alpha, const 
     Domain* d = g->domains[s];
     std::memset(&sv[s], 0, sizeof(mg_solve_stats));
     sv[s].levels = d->nlev;
-    mg_status ps = domain_prepare_sources(d, st, branch[s], alpha[s], kappa[s], o.guard, P.ops[s]);
+    mg_status ps = domain_prepare_sources(d, st, branch[s], alpha[s], kappa[s], o.guard, o.omega,
+                                          P.ops[s]);
     if (ps != MG_OK) return ps;
     P.kappa[s] = (float)kappa[s];
     if (mixed) {

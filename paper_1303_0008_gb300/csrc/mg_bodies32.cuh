@@ -6,6 +6,14 @@
 
 namespace mg {
 
+// sqrt and division of the correction operator: correctly rounded in FP64 (the
+// coarsest inner level), the fast hardware forms in FP32 (the correction only has
+// to be accurate to FP32 precision).
+__device__ __forceinline__ double root_of(double q) { return sqrt(q); }
+__device__ __forceinline__ float root_of(float q) { return q > 0.f ? q * rsqrtf(q) : 0.f; }
+__device__ __forceinline__ double ratio_of(double a, double b) { return a / b; }
+__device__ __forceinline__ float ratio_of(float a, float b) { return __fdividef(a, b); }
+
 // The change of the root D when phi0 moves by e, from the stencils of e and phi0.
 template <typename T>
 __device__ __forceinline__ T delta_D(const StencilT<T>& se, const StencilT<T>& sp, T q0, T g1,
@@ -19,11 +27,11 @@ __device__ __forceinline__ T delta_D(const StencilT<T>& se, const StencilT<T>& s
   const T du = g1 * dA + g2 * dB;
   du_out = du;
   const T q1 = q0 + c3 * du;
-  const T s0 = sqrt(q0 > T(0) ? q0 : T(0));
-  const T s1 = sqrt(q1 > T(0) ? q1 : T(0));
+  const T s0 = root_of(q0 > T(0) ? q0 : T(0));
+  const T s1 = root_of(q1 > T(0) ? q1 : T(0));
   if (q0 >= T(0) && q1 >= T(0)) {
     const T den = s0 + s1;
-    return den > T(0) ? sigma * two * du / den : T(0);
+    return den > T(0) ? ratio_of(sigma * two * du, den) : T(0);
   }
   return sigma * k2 * (s1 - s0);
 }
@@ -134,6 +142,9 @@ __device__ __forceinline__ void b_smooth_colour32(int n, float* __restrict__ e,
                                                          const LevelScalars* __restrict__ sc,
                                                          OpConst32 c, int colour,
     long long blk) {
+  __shared__ float s_mu;
+  if (threadIdx.x == 0) s_mu = (float)sc->lambda;
+  __syncthreads();
   const int hn = n >> 1;
   const long long t = (long long)blk * blockDim.x + threadIdx.x;
   const long long total = (long long)hn * hn * n;
@@ -145,14 +156,11 @@ __device__ __forceinline__ void b_smooth_colour32(int n, float* __restrict__ e,
   const int i = 2 * m + ((colour ^ k) & 1);
   const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
   const long long id = lidx(i, j, k, n);
-  const StencilT<float> se = gather_periodic(e, i, j, k, n);
+  const NbrOff o = nbr_offsets(i, j, k, n);
+  const StencilT<float> se = gather_at(e + id, o);
   float dd = 0.f;
-  if (!c.linear) {
-    const StencilT<float> sp = gather_periodic(phi0, i, j, k, n);
-    dd = dD32(se, sp, q0[id], c);
-  }
-  const float rhs = g[id] + (float)sc->lambda;
-  e[id] = fmaf(-c.h2, dd + rhs, se.sx + se.sy + se.sz) * (1.f / 6.f);
+  if (!c.linear) dd = dD32(se, gather_at(phi0 + id, o), q0[id], c);
+  e[id] = fmaf(-c.h2, dd + (g[id] + s_mu), se.sx + se.sy + se.sz) * (1.f / 6.f);
 }
 
 __device__ __forceinline__ void b_residual_restrict32(

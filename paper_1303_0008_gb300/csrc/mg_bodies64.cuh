@@ -35,14 +35,20 @@ __device__ __forceinline__ void b_smooth_colour64(int n, double* __restrict__ ph
   const double lapnb = s.sx + s.sy + s.sz;
   double acc = fma(lapnb, 1.0 / 6.0, s_c);
   if (f) acc = fma(f[id], -c.h2_6, acc);
+  double v;
   if (c.mode == OP_SQRT) {
     const double B = fma(s.cxy, s.cxy, fma(s.cxz, s.cxz, s.cyz * s.cyz));
     const double q = fma(c.e1h, half_A(s), fma(c.e2, B, src[id]));
-    phi[id] = fma(c.upd_s, sqrt_nonneg(q < 0.0 ? 0.0 : q), acc);
+    v = fma(c.upd_s, sqrt_nonneg(q < 0.0 ? 0.0 : q), acc);
   } else {
     bool g;
-    phi[id] = fma(-c.h2_6, root_D(s, src[id], c, g), acc);
+    v = fma(-c.h2_6, root_D(s, src[id], c, g), acc);
   }
+  if (c.omega != 1.0) {
+    const double old = phi[id];
+    v = fma(c.omega, v - old, old);
+  }
+  phi[id] = v;
 }
 
 __device__ __forceinline__ void b_residual_restrict64(
@@ -212,7 +218,8 @@ __device__ __forceinline__ void b_coarsest64(int n, double* __restrict__ phi,
         const StencilT<double> s = gather_periodic<double>(sphi, i, j, k, n);
         bool g;
         const double D = root_D(s, ssrc[id], c, g);
-        sphi[id] = fma(-c.h2, D + sf[id] + s_lam, s.sx + s.sy + s.sz) * (1.0 / 6.0);
+        const double v = fma(-c.h2, D + sf[id] + s_lam, s.sx + s.sy + s.sz) * (1.0 / 6.0);
+        sphi[id] = (c.omega != 1.0) ? fma(c.omega, v - sphi[id], sphi[id]) : v;
       }
       __syncthreads();
     }

@@ -41,6 +41,7 @@ struct OpConst64 {
   double e1h, c1h;  // 2*e1, 2*c1: the same terms written with A/2
   double h2_6;      // h^2/6
   double upd_s;     // -h^2 k2s / 6: the smoother's coefficient of sqrt(q)
+  double omega;     // relaxation of the pointwise Newton step (1 = the plain step)
   int mode;
 };
 
@@ -83,25 +84,43 @@ struct StencilT {
   T sx, sy, sz, cxy, cxz, cyz;
 };
 
+// Offsets from cell (i,j,k) to its six face neighbours in a periodic n^3 array,
+// x fastest, with the wrap folded in (n <= 1024, so every offset fits in 32 bits).
+struct NbrOff {
+  int xp, xm, yp, ym, zp, zm;
+};
+
+__device__ __forceinline__ NbrOff nbr_offsets(int i, int j, int k, int n) {
+  const int n2 = n * n, n3 = n2 * n;
+  NbrOff o;
+  o.xp = (i + 1 == n) ? 1 - n : 1;
+  o.xm = (i == 0) ? n - 1 : -1;
+  o.yp = (j + 1 == n) ? n - n2 : n;
+  o.ym = (j == 0) ? n2 - n : -n;
+  o.zp = (k + 1 == n) ? n2 - n3 : n2;
+  o.zm = (k == 0) ? n3 - n2 : -n2;
+  return o;
+}
+
+// Face sums and cross differences around the cell at c (a pointer to it).
+template <typename T>
+__device__ __forceinline__ StencilT<T> gather_at(const T* __restrict__ c, const NbrOff& o) {
+  StencilT<T> s;
+  s.sx = c[o.xp] + c[o.xm];
+  s.sy = c[o.yp] + c[o.ym];
+  s.sz = c[o.zp] + c[o.zm];
+  s.cxy = (c[o.xp + o.yp] + c[o.xm + o.ym]) - (c[o.xp + o.ym] + c[o.xm + o.yp]);
+  s.cxz = (c[o.xp + o.zp] + c[o.xm + o.zm]) - (c[o.xp + o.zm] + c[o.xm + o.zp]);
+  s.cyz = (c[o.yp + o.zp] + c[o.ym + o.zm]) - (c[o.yp + o.zm] + c[o.ym + o.zp]);
+  return s;
+}
+
 // Gather the face sums and cross differences of cell (i,j,k) of a periodic n^3
 // array.
 template <typename T>
 __device__ __forceinline__ StencilT<T> gather_periodic(const T* __restrict__ p, int i, int j,
                                                        int k, int n) {
-  const int ip = wrap_up(i, n), im = wrap_dn(i, n);
-  const int jp = wrap_up(j, n), jm = wrap_dn(j, n);
-  const int kp = wrap_up(k, n), km = wrap_dn(k, n);
-  StencilT<T> s;
-  s.sx = p[lidx(ip, j, k, n)] + p[lidx(im, j, k, n)];
-  s.sy = p[lidx(i, jp, k, n)] + p[lidx(i, jm, k, n)];
-  s.sz = p[lidx(i, j, kp, n)] + p[lidx(i, j, km, n)];
-  s.cxy = (p[lidx(ip, jp, k, n)] + p[lidx(im, jm, k, n)]) -
-          (p[lidx(ip, jm, k, n)] + p[lidx(im, jp, k, n)]);
-  s.cxz = (p[lidx(ip, j, kp, n)] + p[lidx(im, j, km, n)]) -
-          (p[lidx(ip, j, km, n)] + p[lidx(im, j, kp, n)]);
-  s.cyz = (p[lidx(i, jp, kp, n)] + p[lidx(i, jm, km, n)]) -
-          (p[lidx(i, jp, km, n)] + p[lidx(i, jm, kp, n)]);
-  return s;
+  return gather_at(p + lidx(i, j, k, n), nbr_offsets(i, j, k, n));
 }
 
 // A/2 with A = (Sx-Sy)^2 + (Sx-Sz)^2 + (Sy-Sz)^2 = 2[a1(a1-a2) + a2^2], a1 = Sx-Sy,

@@ -42,8 +42,8 @@ static const int kMaxCoarsest = 16;  // the coarsest solve runs in one CTA's sha
 
 mg_status domain_create(Domain** out, int n, const mg_options& o) {
   *out = nullptr;
-  if (n < 4 || (n & 1) || n > 2048) {
-    set_error("n must be even and in [4, 2048]");
+  if (n < 4 || (n & 1) || n > 1024) {
+    set_error("n must be even and in [4, 1024]");
     return MG_EINVAL;
   }
   const int nl = num_levels(n, o.coarsest);
@@ -250,11 +250,13 @@ mg_status mixed_solve(Domain* d, const mg_options& o, cudaStream_t st, const OpC
                       int branch, double alpha, double kappa, double tol, mg_solve_stats* s);
 
 mg_status domain_prepare_sources(Domain* d, cudaStream_t st, int branch, double alpha,
-                                 double kappa, int guard, std::vector<OpConst64>& ops) {
+                                 double kappa, int guard, double omega,
+                                 std::vector<OpConst64>& ops) {
   ops.resize(d->nlev);
   DCK(cudaMemsetAsync(d->d_sc, 0, sizeof(LevelScalars) * (2 * d->nlev + 2), st));
   for (int l = 0; l < d->nlev; ++l) {
     ops[l] = make_op64(d->lv[l].n, alpha, kappa, branch);
+    ops[l].omega = omega;
     double a, b;
     src_coefficients(ops[l], kappa, &a, &b);
     launch_affine64(st, d->lv[l].cells, d->lv[l].delta, d->lv[l].src, a, b, ops[l].c3,
@@ -271,7 +273,7 @@ mg_status domain_solve(Domain* d, const mg_options& o, cudaStream_t st, int bran
   s->levels = d->nlev;
   const long long launches0 = tl_launches;
   std::vector<OpConst64> ops;
-  mg_status rs = domain_prepare_sources(d, st, branch, alpha, kappa, o.guard, ops);
+  mg_status rs = domain_prepare_sources(d, st, branch, alpha, kappa, o.guard, o.omega, ops);
   if (rs != MG_OK) return rs;
   cudaEvent_t e0, e1;
   DCK(cudaEventCreate(&e0));

@@ -167,6 +167,7 @@ OpConst64 make_op64(int n, double alpha, double kappa, int branch) {
   c.h2 = h * h;
   c.inv_h2 = (double)n * (double)n;
   c.h2_6 = c.h2 / 6.0;
+  c.omega = 1.0;
   const double h4 = c.h2 * c.h2;
   c.c3 = 4.0 * (1.0 - w) * alpha;
   if (alpha == 0.0) {

@@ -16,6 +16,7 @@
 // The four-colour order uses level coordinates; origins are multiples of the
 // block size, so local and global parities agree.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -135,7 +136,10 @@ __global__ void __launch_bounds__(128) k_patch_smooth(double* __restrict__ phi,
     bool g;
     const double D = root_D(s, src[id], c, g);
     const double rhs = f ? f[id] : 0.0;
-    phi[id] = fma(-c.h2, D + rhs, s.sx + s.sy + s.sz) * (1.0 / 6.0);
+    const double v = fma(-c.h2, D + rhs, s.sx + s.sy + s.sz) * (1.0 / 6.0);
+    phi[id] = (c.omega != 1.0) ? fma(c.omega, v - tile_ctr<B>(tile, i, j, k),
+                                     tile_ctr<B>(tile, i, j, k))
+                               : v;
   }
 }
 
@@ -222,7 +226,7 @@ template <int B>
 __global__ void __launch_bounds__(128) k_patch_prolong(const double* __restrict__ phi_c,
                                                        const double* __restrict__ phihat_c,
                                                        const int* __restrict__ nbr,
-                                                       double* __restrict__ phi) {
+                                                       double* __restrict__ phi, double theta) {
   constexpr int H = B / 2, HT = H + 2, HC = H * H * H, BC = B * B * B;
   __shared__ double corr[HT * HT * HT];
   const int p = blockIdx.x;
@@ -247,7 +251,7 @@ __global__ void __launch_bounds__(128) k_patch_prolong(const double* __restrict_
     const int I1 = I0 + ((i & 1) ? 1 : -1), J1 = J0 + ((j & 1) ? 1 : -1), K1 = K0 + ((k & 1) ? 1 : -1);
     const double v = 27.0 * e(I0, J0, K0) + 9.0 * (e(I1, J0, K0) + e(I0, J1, K0) + e(I0, J0, K1)) +
                      3.0 * (e(I1, J1, K0) + e(I1, J0, K1) + e(I0, J1, K1)) + e(I1, J1, K1);
-    phi[(long long)p * BC + t] += v * (1.0 / 64.0);
+    phi[(long long)p * BC + t] += v * (theta / 64.0);
   }
 }
 
@@ -537,15 +541,17 @@ struct PatchCycle {
     const int P = pl->count;
     dispatch(
         m,
-        [&] { k_patch_prolong<8><<<P, 128, 0, st>>>(phi(1), pl->phihat_c[1], pl->d_nbr, phi(0)); },
-        [&] { k_patch_prolong<4><<<P, 128, 0, st>>>(phi(2), pl->phihat_c[2], pl->d_nbr, phi(1)); },
+        [&] { k_patch_prolong<8><<<P, 128, 0, st>>>(phi(1), pl->phihat_c[1], pl->d_nbr, phi(0), o->patch_cgc); },
+        [&] { k_patch_prolong<4><<<P, 128, 0, st>>>(phi(2), pl->phihat_c[2], pl->d_nbr, phi(1), o->patch_cgc); },
         [&] {});
     count_launches(1);
   }
 
+  int mlev() const { return o->patch_mg_levels; }
+
   void descend(int m) const {
-    if (m == 2) {
-      smooth(2, o->patch_coarse_sweeps);
+    if (m == mlev() - 1) {
+      smooth(m, o->patch_coarse_sweeps);
       return;
     }
     smooth(m, o->nu_pre);
@@ -558,14 +564,16 @@ struct PatchCycle {
 
   void part_a() const {
     smooth(0, o->nu_pre);
-    residual(0, true);
+    residual(0, mlev() > 1);
     cudaMemcpyAsync(pl->h_sc, pl->d_sc, sizeof(LevelScalars), cudaMemcpyDeviceToHost, st);
   }
 
   void part_b() const {
-    fas_rhs(1);
-    descend(1);
-    prolong(0);
+    if (mlev() > 1) {
+      fas_rhs(1);
+      descend(1);
+      prolong(0);
+    }
     smooth(0, o->nu_post);
   }
 };
@@ -585,6 +593,7 @@ mg_status patch_level_solve(mg_grid* g, int level, int branch, double alpha, dou
   PatchCycle cyc{pl, &g->opt, st, {}};
   for (int m = 0; m < 3; ++m) {
     cyc.ops[m] = make_op64(pl->nside >> m, alpha, kappa, branch);
+    cyc.ops[m].omega = g->opt.omega_patch;
     double a, b;
     src_coefficients(cyc.ops[m], kappa, &a, &b);
     const int bm = block_of(m);
@@ -672,6 +681,14 @@ mg_status patch_level_solve(mg_grid* g, int level, int branch, double alpha, dou
   }
   pl->last_cycles = (int)hist.size() - 1;
   pl->last_res = hist.empty() ? 0.0 : hist.back();
+  pl->last_status = result;
+  pl->last_hist = hist;
+  if (result == MG_ENOCONV) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), " after %d cycles (residual %.3e -> %.3e)", (int)hist.size() - 1,
+                  first, hist.empty() ? 0.0 : hist.back());
+    set_error("refinement level " + std::to_string(level) + ": no convergence" + buf);
+  }
   if (ga) cudaGraphExecDestroy(ga);
   if (gb) cudaGraphExecDestroy(gb);
   return result;

@@ -72,6 +72,8 @@ struct PatchLevel {
   double* d_coarse_parent = nullptr;  // level 1: the domain field restricted once
   int last_cycles = 0;
   double last_res = 0.0;
+  int last_status = 0;
+  std::vector<double> last_hist;
 };
 
 struct BatchState;

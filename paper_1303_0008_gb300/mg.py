@@ -35,7 +35,9 @@ class mg_options(ctypes.Structure):
                 ("inner_cycles", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("coarse_sweeps", ctypes.c_int), ("coarse_drop", ctypes.c_double),
                 ("time_kernels", ctypes.c_int), ("guard", ctypes.c_int),
-                ("patch_coarse_sweeps", ctypes.c_int), ("fuse_coarse", ctypes.c_int)]
+                ("patch_coarse_sweeps", ctypes.c_int), ("fuse_coarse", ctypes.c_int),
+                ("omega", ctypes.c_double), ("omega_patch", ctypes.c_double),
+                ("patch_mg_levels", ctypes.c_int), ("patch_cgc", ctypes.c_double)]
 
 
 class mg_solve_stats(ctypes.Structure):
@@ -84,6 +86,10 @@ _SIGS = {
     "mg_op_prolong_correct": (_I, [_I, _P, _P, _P, _P]),
     "mg_op_force": (_I, [_I, _P, _P, _P]),
     "mg_op_residual_noalloc": (_I, [_I, _P, _P, _P, _I, _F, _F, _P, _D, _P]),
+    "mg_get_options": (_I, [_P, ctypes.POINTER(mg_options)]),
+    "mg_get_level_stats": (_I, [_P, _I, ctypes.POINTER(mg_solve_stats)]),
+    "mg_set_options": (_I, [_P, ctypes.POINTER(mg_options)]),
+    "mg_autotune": (_I, [_P, _I, _F, _F, _F, ctypes.c_char_p, _I, ctypes.POINTER(mg_options), _D]),
 }
 
 
@@ -231,6 +237,36 @@ def mg_get_force(g, level: int, patch: int, out):
     p, dev, _ = _arr(out, writable=True)
     _check(lib().mg_get_force(g, level, patch, p, dev), "mg_get_force")
     return out
+
+
+def mg_get_level_stats(g, level):
+    st = mg_solve_stats()
+    _check(lib().mg_get_level_stats(g, level, ctypes.byref(st)), "mg_get_level_stats")
+    return st.as_dict()
+
+
+def mg_get_options(g) -> mg_options:
+    o = mg_options()
+    _check(lib().mg_get_options(g, ctypes.byref(o)), "mg_get_options")
+    return o
+
+
+def mg_set_options(g, opt: mg_options):
+    _check(lib().mg_set_options(g, ctypes.byref(opt)), "mg_set_options")
+
+
+def mg_autotune(g, branch, alpha, kappa, tol, cache_path=None, use_cache=True):
+    """Tune sweep counts on the handle's problem; returns (options, seconds)."""
+    o = mg_options()
+    t = ctypes.c_double()
+    path = cache_path.encode() if cache_path else None
+    _check(lib().mg_autotune(g, branch, alpha, kappa, tol, path, int(bool(use_cache)),
+                             ctypes.byref(o), ctypes.byref(t)), "mg_autotune")
+    return o, t.value
+
+
+def options_dict(o: mg_options) -> dict:
+    return {name: getattr(o, name) for name, _ in mg_options._fields_}
 
 
 def mg_destroy_grid(g):
