@@ -90,7 +90,9 @@ typedef struct {
   int inner_cycles;  /* mixed: FP32 V-cycles per FP64 correction (default 3) */
   int use_graphs;    /* capture each V-cycle in a CUDA graph (default 1) */
   int coarse_sweeps; /* cap on coarsest-level sweeps (default 200) */
-  double coarse_drop;/* coarsest solve stops when its residual fell by this (1e-6) */
+  double coarse_drop;/* coarsest solve stops when its residual fell by this (default
+                        1e-2: a tighter coarsest solve leaves the V-cycle count of the
+                        128^3 lognormal solves unchanged and only costs time) */
   int time_kernels;  /* 1: time every launch of the finest-level smoother with CUDA
                         events on the handle's stream (stats.kernel_ms); default 0 */
   mg_guard guard;    /* default MG_GUARD_FLOOR */
@@ -105,6 +107,10 @@ typedef struct {
                         2 (8^3 and 4^3 per patch) or 3 (down to 2^3; default) */
   double patch_cgc;  /* scale of the coarse-grid correction on refinement unions
                         (1 = the full FAS correction; default 1) */
+  int sweep32;       /* mixed precision: 1 runs each pair of FP32 correction sweeps on
+                        levels with n >= 32, n % 4 == 0 as two one-launch four-colour
+                        sweeps (same arithmetic, same bits as the per-colour launches);
+                        0 keeps four launches per sweep (default). */
 } mg_options;
 
 typedef struct {

@@ -53,7 +53,7 @@ void mg_default_options(mg_options* opt) {
   opt->inner_cycles = 3;
   opt->use_graphs = 1;
   opt->coarse_sweeps = 200;
-  opt->coarse_drop = 1e-6;
+  opt->coarse_drop = 1e-2;
   opt->time_kernels = 0;
   opt->guard = MG_GUARD_FLOOR;
   opt->patch_coarse_sweeps = 8;
@@ -62,6 +62,7 @@ void mg_default_options(mg_options* opt) {
   opt->omega_patch = 1.0;
   opt->patch_mg_levels = 3;
   opt->patch_cgc = 1.0;
+  opt->sweep32 = 0;
 }
 
 static mg_status check_options(const mg_options& o) {
@@ -82,6 +83,7 @@ static mg_status check_options(const mg_options& o) {
     MG_FAIL(MG_EINVAL, "options: omega and omega_patch must be in (0, 1]");
   if (o.patch_mg_levels < 1 || o.patch_mg_levels > 3) MG_FAIL(MG_EINVAL, "options: patch_mg_levels");
   if (!(o.patch_cgc > 0.0 && o.patch_cgc <= 1.0)) MG_FAIL(MG_EINVAL, "options: patch_cgc");
+  if (o.sweep32 != 0 && o.sweep32 != 1) MG_FAIL(MG_EINVAL, "options: sweep32");
   return MG_OK;
 }
 

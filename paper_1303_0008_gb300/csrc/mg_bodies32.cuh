@@ -36,11 +36,43 @@ __device__ __forceinline__ T delta_D(const StencilT<T>& se, const StencilT<T>& s
   return sigma * k2 * (s1 - s0);
 }
 
+// The FP32 root change with every rounding spelled out (no contraction left to
+// the compiler), so that the per-colour kernels and the one-launch sweep, which
+// evaluates two cells per packed FP32x2 instruction, give the same bits.
+// Both forms are evaluated and one is selected (no branch): 2 du / (s0 + s1) where
+// both discriminants are non-negative, k2 (s1 - s0) of the guarded roots otherwise.
+__device__ __forceinline__ float root_change32(float q0, float q1, float du, const OpConst32& c) {
+  const float s0 = q0 > 0.f ? __fmul_rn(q0, rsqrtf(q0)) : 0.f;
+  const float s1 = q1 > 0.f ? __fmul_rn(q1, rsqrtf(q1)) : 0.f;
+  const float den = __fadd_rn(s0, s1);
+  const float conj = den > 0.f ? __fdividef(__fmul_rn(c.sigma2, du), den) : 0.f;
+  const float diff = __fmul_rn(c.sk2, __fsub_rn(s1, s0));
+  return (q0 >= 0.f && q1 >= 0.f) ? conj : diff;
+}
+
 __device__ __forceinline__ float dD32(const StencilT<float>& se, const StencilT<float>& sp,
                                       float q0, const OpConst32& c) {
   if (c.linear) return 0.f;
-  float du;
-  return delta_D<float>(se, sp, q0, c.g1, c.g2, c.c3, c.k2, c.sigma, du);
+  const float a1e = __fsub_rn(se.sx, se.sy), a2e = __fsub_rn(se.sx, se.sz),
+              a3e = __fsub_rn(se.sy, se.sz);
+  const float a1p = __fsub_rn(sp.sx, sp.sy), a2p = __fsub_rn(sp.sx, sp.sz),
+              a3p = __fsub_rn(sp.sy, sp.sz);
+  const float dA = __fmaf_rn(a3e, __fmaf_rn(2.f, a3p, a3e),
+                             __fmaf_rn(a2e, __fmaf_rn(2.f, a2p, a2e),
+                                       __fmul_rn(a1e, __fmaf_rn(2.f, a1p, a1e))));
+  const float dB = __fmaf_rn(se.cyz, __fmaf_rn(2.f, sp.cyz, se.cyz),
+                             __fmaf_rn(se.cxz, __fmaf_rn(2.f, sp.cxz, se.cxz),
+                                       __fmul_rn(se.cxy, __fmaf_rn(2.f, sp.cxy, se.cxy))));
+  const float du = __fmaf_rn(c.g2, dB, __fmul_rn(c.g1, dA));
+  return root_change32(q0, __fmaf_rn(c.c3, du, q0), du, c);
+}
+
+// Gauss-Seidel value of one cell of N(e) = g + mu: (face sum - h^2 (dD + g + mu)) / 6.
+__device__ __forceinline__ float gs_value32(const StencilT<float>& se, float dd, float g, float mu,
+                                            const OpConst32& c) {
+  return __fmul_rn(__fmaf_rn(-c.h2, __fadd_rn(dd, __fadd_rn(g, mu)),
+                             __fadd_rn(__fadd_rn(se.sx, se.sy), se.sz)),
+                   1.f / 6.f);
 }
 
 __device__ __forceinline__ void b_residual_handoff64(
@@ -160,7 +192,7 @@ __device__ __forceinline__ void b_smooth_colour32(int n, float* __restrict__ e,
   const StencilT<float> se = gather_at(e + id, o);
   float dd = 0.f;
   if (!c.linear) dd = dD32(se, gather_at(phi0 + id, o), q0[id], c);
-  e[id] = fmaf(-c.h2, dd + (g[id] + s_mu), se.sx + se.sy + se.sz) * (1.f / 6.f);
+  e[id] = gs_value32(se, dd, g[id], s_mu, c);
 }
 
 __device__ __forceinline__ void b_residual_restrict32(

@@ -52,6 +52,8 @@ struct OpConst32 {
   float c3;       // 4(1-w) alpha
   float k2;       // 2/c3 (0 when alpha == 0)
   float sigma;    // +1 physical root, -1 the other one
+  float sigma2;   // 2 sigma
+  float sk2;      // sigma k2
   int linear;     // alpha == 0
 };
 

@@ -150,4 +150,11 @@ void launch_subcycle64(cudaStream_t st, const SubCycleArgs& a);
 void launch_subcycle32(cudaStream_t st, const SubCycleArgs& a);
 void init_subcycle();
 
+// One-launch four-colour sweep of the FP32 correction operator (mg_sweep32.cu):
+// reads e_in, writes every cell of e_out; n >= 32 and n % 4 == 0.
+bool sweep32_eligible(int n);
+void init_sweep32();
+void launch_sweep32(cudaStream_t st, int n, const float* e_in, float* e_out, const float* phi0,
+                    const float* q0, const float* g, const LevelScalars* sc, const OpConst32& c);
+
 }  // namespace mg

@@ -137,6 +137,8 @@ OpConst32 make_op32(int n, double alpha, int branch) {
   c.k2 = c.linear ? 0.f : (float)(2.0 / c3);
   const bool physical = (branch == 0) || ((branch > 0) == (alpha > 0));
   c.sigma = physical ? 1.f : -1.f;
+  c.sigma2 = 2.f * c.sigma;
+  c.sk2 = c.sigma * c.k2;
   return c;
 }
 
@@ -148,7 +150,8 @@ void mixed_release(Domain* d) {
     cudaFree(L.q0);
     cudaFree(L.rhs);
     cudaFree(L.src32);
-    L.e = L.ehat = L.phi0 = L.q0 = L.rhs = L.src32 = nullptr;
+    cudaFree(L.e2);
+    L.e = L.ehat = L.phi0 = L.q0 = L.rhs = L.src32 = L.e2 = nullptr;
   }
   d->mixed_ready = false;
 }
@@ -164,6 +167,7 @@ static mg_status mixed_prepare(Domain* d) {
     ok = ok && cudaMalloc(&L.q0, b) == cudaSuccess;
     ok = ok && cudaMalloc(&L.rhs, b) == cudaSuccess;
     if (l > 0) ok = ok && cudaMalloc(&L.ehat, b) == cudaSuccess;
+    if (sweep32_eligible(L.n)) ok = ok && cudaMalloc(&L.e2, b) == cudaSuccess;
   }
   if (!ok) {
     mixed_release(d);
@@ -176,6 +180,7 @@ static mg_status mixed_prepare(Domain* d) {
                          4 * sizeof(double) * 4096);
     attr = true;
   }
+  init_sweep32();
   d->mixed_ready = true;
   return MG_OK;
 }
@@ -195,6 +200,19 @@ struct CycleMixed {
 
   void smooth(int l, int sweeps) const {
     Level& L = d->lv[l];
+    if (o->sweep32 && L.e2) {
+      // pairs of one-launch sweeps e -> e2 -> e; an odd last sweep goes e -> e2
+      // and is copied back
+      for (int s = 0; s < sweeps; s += 2) {
+        launch_sweep32(st, L.n, L.e, L.e2, L.phi0, L.q0, L.rhs, sc32(l), ops32[l]);
+        if (s + 1 < sweeps)
+          launch_sweep32(st, L.n, L.e2, L.e, L.phi0, L.q0, L.rhs, sc32(l), ops32[l]);
+        else
+          cudaMemcpyAsync(L.e, L.e2, sizeof(float) * (size_t)L.cells, cudaMemcpyDeviceToDevice,
+                          st);
+      }
+      return;
+    }
     const long long per = (long long)(L.n / 2) * (L.n / 2) * L.n;
     for (int s = 0; s < sweeps; ++s)
       for (int colour = 0; colour < 4; ++colour)

@@ -27,6 +27,7 @@ struct Level {
   float* q0 = nullptr;       // discriminant at the expansion point
   float* rhs = nullptr;      // right-hand side of N(e) = rhs (+ mu)
   float* src32 = nullptr;    // kappa * delta in FP32 (coarse levels)
+  float* e2 = nullptr;       // second correction buffer of the one-launch sweep
 };
 
 struct Domain {
