@@ -85,9 +85,8 @@ __device__ __forceinline__ void b_residual_handoff64(
   Partial p;
   partial_init(p);
   if (t < cells) {
-    const int i = (int)(t % n);
-    const int j = (int)((t / n) % n);
-    const int k = (int)(t / ((long long)n * n));
+    int i, j, k;
+    split3((unsigned)t, n, i, j, k);
     const StencilT<double> s = gather_periodic(phi, i, j, k, n);
     double q = 1.0, D;
     bool guard = false;
@@ -133,9 +132,8 @@ __device__ __forceinline__ void b_restrict32(int nc, const float* __restrict__ f
   const long long cells = (long long)nc * nc * nc;
   const long long t = (long long)blk * blockDim.x + threadIdx.x;
   if (t >= cells) return;
-  const int I = (int)(t % nc);
-  const int J = (int)((t / nc) % nc);
-  const int K = (int)(t / ((long long)nc * nc));
+  int I, J, K;
+  split3((unsigned)t, nc, I, J, K);
   float s = 0.f;
 #pragma unroll
   for (int ch = 0; ch < 8; ++ch)
@@ -155,9 +153,8 @@ __device__ __forceinline__ void b_q0_prep32(int n, const float* __restrict__ phi
     q0[t] = 1.f;
     return;
   }
-  const int i = (int)(t % n);
-  const int j = (int)((t / n) % n);
-  const int k = (int)(t / ((long long)n * n));
+  int i, j, k;
+  split3((unsigned)t, n, i, j, k);
   const StencilT<float> s = gather_periodic(phi0, i, j, k, n);
   const float a1 = s.sx - s.sy, a2 = s.sx - s.sz, a3 = s.sy - s.sz;
   const float A = a1 * a1 + a2 * a2 + a3 * a3;
@@ -181,10 +178,8 @@ __device__ __forceinline__ void b_smooth_colour32(int n, float* __restrict__ e,
   const long long t = (long long)blk * blockDim.x + threadIdx.x;
   const long long total = (long long)hn * hn * n;
   if (t >= total) return;
-  const int m = (int)(t % hn);
-  const long long rest = t / hn;
-  const int jj = (int)(rest % hn);
-  const int k = (int)(rest / hn);
+  int m, jj, k;
+  split3((unsigned)t, hn, m, jj, k);
   const int i = 2 * m + ((colour ^ k) & 1);
   const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
   const long long id = lidx(i, j, k, n);
@@ -207,9 +202,8 @@ __device__ __forceinline__ void b_residual_restrict32(
   Partial p;
   partial_init(p);
   if (t < ccells) {
-    const int I = (int)(t % nc);
-    const int J = (int)((t / nc) % nc);
-    const int K = (int)(t / ((long long)nc * nc));
+    int I, J, K;
+    split3((unsigned)t, nc, I, J, K);
     float se_sum = 0.f, sr = 0.f;
 #pragma unroll 1
     for (int ch = 0; ch < 8; ++ch) {
@@ -247,9 +241,8 @@ __device__ __forceinline__ void b_fas_rhs32(int nc, const float* __restrict__ e_
   const long long t = (long long)blk * blockDim.x + threadIdx.x;
   if (t == 0) coarse_sc->lambda = 0.0;
   if (t >= cells) return;
-  const int i = (int)(t % nc);
-  const int j = (int)((t / nc) % nc);
-  const int k = (int)(t / ((long long)nc * nc));
+  int i, j, k;
+  split3((unsigned)t, nc, i, j, k);
   const StencilT<float> se = gather_periodic(e_c, i, j, k, nc);
   float dd = 0.f;
   if (!c.linear) {
@@ -269,9 +262,8 @@ __device__ __forceinline__ void b_prolong_correct32(int nc, const float* __restr
   const long long cells = (long long)nf * nf * nf;
   const long long t = (long long)blk * blockDim.x + threadIdx.x;
   if (t >= cells) return;
-  const int i = (int)(t % nf);
-  const int j = (int)((t / nf) % nf);
-  const int k = (int)(t / ((long long)nf * nf));
+  int i, j, k;
+  split3((unsigned)t, nf, i, j, k);
   const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
   const int I1 = (i & 1) ? wrap_up(I0, nc) : wrap_dn(I0, nc);
   const int J1 = (j & 1) ? wrap_up(J0, nc) : wrap_dn(J0, nc);

@@ -24,10 +24,8 @@ __device__ __forceinline__ void b_smooth_colour64(int n, double* __restrict__ ph
   const long long t = (long long)blk * blockDim.x + threadIdx.x;
   const long long total = (long long)hn * hn * n;
   if (t >= total) return;
-  const int m = (int)(t % hn);
-  const long long rest = t / hn;
-  const int jj = (int)(rest % hn);
-  const int k = (int)(rest / hn);
+  int m, jj, k;
+  split3((unsigned)t, hn, m, jj, k);
   const int i = 2 * m + ((colour ^ k) & 1);
   const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
   const long long id = lidx(i, j, k, n);
@@ -62,9 +60,8 @@ __device__ __forceinline__ void b_residual_restrict64(
   Partial p;
   partial_init(p);
   if (t < ccells) {
-    const int I = (int)(t % nc);
-    const int J = (int)((t / nc) % nc);
-    const int K = (int)(t / ((long long)nc * nc));
+    int I, J, K;
+    split3((unsigned)t, nc, I, J, K);
     double sphi = 0.0, sd = 0.0;
 #pragma unroll 1
     for (int ch = 0; ch < 8; ++ch) {
@@ -119,9 +116,8 @@ __device__ __forceinline__ void b_fas_rhs64(int nc, const double* __restrict__ p
   const long long t = (long long)blk * blockDim.x + threadIdx.x;
   if (t == 0) coarse_sc->lambda = 0.0;
   if (t >= cells) return;
-  const int i = (int)(t % nc);
-  const int j = (int)((t / nc) % nc);
-  const int k = (int)(t / ((long long)nc * nc));
+  int i, j, k;
+  split3((unsigned)t, nc, i, j, k);
   const StencilT<double> s = gather_periodic(phi_c, i, j, k, nc);
   bool g;
   const double D = root_D(s, src_c[t], c, g);
@@ -138,9 +134,8 @@ __device__ __forceinline__ void b_prolong_correct64(int nc, const double* __rest
   const long long cells = (long long)nf * nf * nf;
   const long long t = (long long)blk * blockDim.x + threadIdx.x;
   if (t >= cells) return;
-  const int i = (int)(t % nf);
-  const int j = (int)((t / nf) % nf);
-  const int k = (int)(t / ((long long)nf * nf));
+  int i, j, k;
+  split3((unsigned)t, nf, i, j, k);
   const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
   const int I1 = (i & 1) ? wrap_up(I0, nc) : wrap_dn(I0, nc);
   const int J1 = (j & 1) ? wrap_up(J0, nc) : wrap_dn(J0, nc);

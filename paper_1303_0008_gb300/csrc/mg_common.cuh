@@ -68,6 +68,24 @@ struct LevelScalars {
   unsigned long long floored;  // cells whose source was held at the real-root bound
 };
 
+// Split a cell index t (< 2^31; grids have n <= 1024) into (t % d, (t / d) % d,
+// t / d^2) with 32-bit arithmetic; shifts and masks when d is a power of two.
+__device__ __forceinline__ void split3(unsigned t, int d, int& i, int& j, int& k) {
+  const unsigned ud = (unsigned)d;
+  if ((ud & (ud - 1u)) == 0u) {
+    const int s = __ffs(d) - 1;
+    const unsigned r = t >> s;
+    i = (int)(t & (ud - 1u));
+    j = (int)(r & (ud - 1u));
+    k = (int)(r >> s);
+  } else {
+    const unsigned r = t / ud, r2 = r / ud;
+    i = (int)(t - r * ud);
+    j = (int)(r - r2 * ud);
+    k = (int)r2;
+  }
+}
+
 __device__ __forceinline__ int wrap_up(int i, int n) { return (i + 1 == n) ? 0 : i + 1; }
 __device__ __forceinline__ int wrap_dn(int i, int n) { return (i == 0) ? n - 1 : i - 1; }
 
