@@ -89,7 +89,9 @@ typedef struct {
   int max_cycles;    /* V-cycles (FP64) or outer corrections (mixed); default 100 */
   int inner_cycles;  /* mixed: FP32 V-cycles per FP64 correction (default 3) */
   int use_graphs;    /* capture each V-cycle in a CUDA graph (default 1) */
-  int coarse_sweeps; /* cap on coarsest-level sweeps (default 200) */
+  int coarse_sweeps; /* cap on coarsest-level sweeps (default 4: the 4^3 coarsest problem
+                        converges slowly per sweep, and more sweeps leave the V-cycle
+                        count of the 128^3 lognormal solves unchanged) */
   double coarse_drop;/* coarsest solve stops when its residual fell by this (default
                         1e-2: a tighter coarsest solve leaves the V-cycle count of the
                         128^3 lognormal solves unchanged and only costs time) */

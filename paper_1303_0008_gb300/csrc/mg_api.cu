@@ -52,7 +52,7 @@ void mg_default_options(mg_options* opt) {
   opt->max_cycles = 100;
   opt->inner_cycles = 3;
   opt->use_graphs = 1;
-  opt->coarse_sweeps = 200;
+  opt->coarse_sweeps = 4;
   opt->coarse_drop = 1e-2;
   opt->time_kernels = 0;
   opt->guard = MG_GUARD_FLOOR;
