@@ -4,7 +4,8 @@
 
 C1  32^3 top-hat (delta 10 in radius 4 cells), r_V = 8 cells, FP64
 C2  128^3 lognormal (sigma 1.5), r_V = 2, 8, 32 cells x both signs, FP64
-C3  256^3 lognormal (sigma 2.0) + two levels of 8^3 patches (delta > 20, > 80), alpha*kappa = 1e-3, FP64
+C3  256^3 lognormal + 8^3 patches over delta > 20 (then > 80): sigma 2.0 at alpha*kappa = 1e-3
+    and sigma 1.0 at r_V = 8 cells, FP64
 C4  512^3 lognormal (sigma 2.0), r_V = 16 cells: mixed vs FP64
 C5  64 independent solves of 32..128^3, mixed, batched
 Every solve goes to max|d - lambda| < 1e-8 from phi = 0.  Each config prints one
@@ -79,33 +80,30 @@ def c2(mg, I, reps):
 def c3(mg, I, reps):
     import numpy as np
     import torch
-    h = I.refined_hierarchy(256, 2.0, 1303)
-    alpha = 1e-3
-    g = mg.mg_create_grid(256, mg.options())
-    res = {"config": "C3", "patches": [len(L["origins"]) for L in h["levels"]]}
-    try:
-        mg.mg_set_stream(g, torch.cuda.current_stream())
-        mg.mg_set_density(g, 0, -1, h["delta0"])
-        for lvl, L in enumerate(h["levels"], start=1):
-            mg.mg_add_patches(g, lvl, L["origins"])
-            mg.mg_set_density(g, lvl, -1, np.ascontiguousarray(L["delta"]))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st = mg.mg_solve(g, 0, alpha, 1.0, TOL)
-        torch.cuda.synchronize()
-        res["seconds_all_levels"] = time.perf_counter() - t0
-        res["domain_ms"] = 1e3 * st["wall_s"]
-        res["domain_cycles"] = st["cycles"]
-        phi0 = np.empty_like(h["delta0"])
-        mg.mg_get_field(g, 0, -1, phi0)
-        phis = []
-        for lvl, L in enumerate(h["levels"], start=1):
-            p = np.empty((len(L["origins"]), 8, 8, 8))
-            mg.mg_get_field(g, lvl, -1, p)
-            phis.append(p)
-    finally:
-        mg.mg_destroy_grid(g)
-    res["cells"] = [256 ** 3, int(phis[0].size), int(phis[1].size)]
+    res = {"config": "C3", "variants": []}
+    for sigma, alpha in ((2.0, 1e-3), (1.0, I.alpha_kappa_for_rv(8.0))):
+        h = I.refined_hierarchy(256, sigma, 1303)
+        levels = [L for L in h["levels"] if len(L["origins"])]
+        g = mg.mg_create_grid(256, mg.options())
+        v = {"sigma": sigma, "alpha_kappa": alpha, "patches": [len(L["origins"]) for L in levels]}
+        try:
+            mg.mg_set_stream(g, torch.cuda.current_stream())
+            mg.mg_set_density(g, 0, -1, h["delta0"])
+            for lvl, L in enumerate(levels, start=1):
+                mg.mg_add_patches(g, lvl, L["origins"])
+                mg.mg_set_density(g, lvl, -1, np.ascontiguousarray(L["delta"]))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = mg.mg_solve(g, 0, alpha, 1.0, TOL)
+            torch.cuda.synchronize()
+            v["seconds_all_levels"] = time.perf_counter() - t0
+            v["domain_ms"] = 1e3 * st["wall_s"]
+            v["domain_cycles"] = st["cycles"]
+            v["level_cycles"] = [mg.mg_get_level_stats(g, lvl)["cycles"]
+                                 for lvl in range(1, len(levels) + 1)]
+        finally:
+            mg.mg_destroy_grid(g)
+        res["variants"].append(v)
     return res
 
 

@@ -22,38 +22,46 @@ def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-def test_c3_refined_levels_full_size():
-    """256^3 domain (sigma 2.0) with 72,167 level-1 and 4,449 level-2 patches and
-    alpha*kappa = 1e-3.  The level-1 density reaches delta = 3382 with 10% noise at
-    the cell scale; from alpha*kappa ~ 5e-3 up, alpha*kappa*delta ~ 16 there makes the
-    linearised operator strongly anisotropic cell by cell and the FAS correction of
-    the 8^3 -> 4^3 -> 2^3 union hierarchy diverges."""
-    h = I.refined_hierarchy(256, 2.0, 1303)
-    alpha = 1e-3
-    l1, l2 = h["levels"]
-    assert len(l1["origins"]) > 1000 and len(l2["origins"]) > 100
+@pytest.mark.parametrize("sigma,alpha,min_patches", [(2.0, 1e-3, (60000, 4000)),
+                                                     (1.0, 0.3, (3000,))])
+def test_c3_refined_levels_full_size(sigma, alpha, min_patches):
+    """256^3 domain with two refinement criteria (delta > 20, then > 80).
+
+    sigma 2.0 gives 72,167 level-1 and 4,449 level-2 patches; the level-1 density
+    reaches delta = 3382 with 10% noise at the cell scale, and from alpha*kappa ~ 3e-3
+    up, alpha*kappa*delta ~ 16 there makes the linearised operator strongly
+    anisotropic cell by cell and the union FAS correction diverges, so this case
+    runs at alpha*kappa = 1e-3.  sigma 1.0 gives 3,124 level-1 patches (no level 2)
+    and runs at r_V = 8 cells (alpha*kappa = 0.3)."""
+    h = I.refined_hierarchy(256, sigma, 1303)
+    levels = h["levels"]
+    counts = [len(L["origins"]) for L in levels if len(L["origins"])]
+    assert len(counts) == len(min_patches)
+    assert all(c > m for c, m in zip(counts, min_patches))
     g = mg.mg_create_grid(256)
+    phis = []
     try:
         mg.mg_set_density(g, 0, -1, h["delta0"])
-        for lvl, L in enumerate(h["levels"], start=1):
+        for lvl, L in enumerate(levels[:len(counts)], start=1):
             mg.mg_add_patches(g, lvl, L["origins"])
             mg.mg_set_density(g, lvl, -1, np.ascontiguousarray(L["delta"]))
-        st = mg.mg_solve(g, 0, alpha, 1.0, TOL)
+        mg.mg_solve(g, 0, alpha, 1.0, TOL)
         phi0 = np.empty_like(h["delta0"])
         mg.mg_get_field(g, 0, -1, phi0)
-        p1 = np.empty((len(l1["origins"]), 8, 8, 8))
-        p2 = np.empty((len(l2["origins"]), 8, 8, 8))
-        mg.mg_get_field(g, 1, -1, p1)
-        mg.mg_get_field(g, 2, -1, p2)
+        for lvl, L in enumerate(levels[:len(counts)], start=1):
+            p = np.empty((len(L["origins"]), 8, 8, 8))
+            mg.mg_get_field(g, lvl, -1, p)
+            phis.append(p)
     finally:
         mg.mg_destroy_grid(g)
     d0, _ = O.residual(phi0, h["delta0"], alpha, 1.0)
     assert np.abs(d0 - d0.mean()).max() < TOL
-    d1, _ = O.patch_residual(256, 1, l1["origins"], p1, l1["delta"], phi0, alpha, 1.0)
-    assert np.abs(d1).max() < TOL
-    d2, _ = O.patch_residual(256, 2, l2["origins"], p2, l2["delta"], p1, alpha, 1.0,
-                             parent_org=l1["origins"])
-    assert np.abs(d2).max() < TOL
+    parent, parent_org = phi0, None
+    for lvl, (L, p) in enumerate(zip(levels, phis), start=1):
+        d, _ = O.patch_residual(256, lvl, L["origins"], p, L["delta"], parent, alpha, 1.0,
+                                parent_org=parent_org)
+        assert np.abs(d).max() < TOL, lvl
+        parent, parent_org = p, L["origins"]
 
 
 def test_c4_512_mixed_and_fp64():
