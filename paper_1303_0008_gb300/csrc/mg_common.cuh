@@ -68,6 +68,19 @@ struct LevelScalars {
   unsigned long long floored;  // cells whose source was held at the real-root bound
 };
 
+// Programmatic dependent launch.  Kernels launched with launch_k() may start
+// while the grid before them in the stream is still finishing; each such kernel
+// opens a PdlScope first, which waits until that grid has completed and its
+// writes are visible (griddepcontrol.wait), and on exit lets the next grid
+// begin launching (griddepcontrol.launch_dependents).  What overlaps is launch
+// latency and the scheduling of CTAs, never a kernel's memory accesses.
+struct PdlScope {
+  __device__ __forceinline__ PdlScope() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+  __device__ __forceinline__ ~PdlScope() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  }
+};
+
 // Split a cell index t (< 2^31; grids have n <= 1024) into (t % d, (t / d) % d,
 // t / d^2) with 32-bit arithmetic; shifts and masks when d is a power of two.
 __device__ __forceinline__ void split3(unsigned t, int d, int& i, int& j, int& k) {

@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(256) k_smooth_colour64(int n, double* __restri
                                                          const double* __restrict__ f,
                                                          const LevelScalars* __restrict__ sc,
                                                          OpConst64 c, int colour) {
+  PdlScope pdl_scope;
   b_smooth_colour64(n, phi, src, f, sc, c, colour, blockIdx.x);
 }
 
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(256) k_residual64(int n, const double* __restr
                                                     const double* __restrict__ f,
                                                     double* __restrict__ dout, OpConst64 c,
                                                     Partial* __restrict__ partials) {
+  PdlScope pdl_scope;
   const long long cells = (long long)n * n * n;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   Partial p;
@@ -61,6 +63,7 @@ __global__ void __launch_bounds__(256) k_residual_restrict64(
     int nf, const double* __restrict__ phi, const double* __restrict__ src,
     const double* __restrict__ f, OpConst64 c, double* __restrict__ phi_c,
     double* __restrict__ phihat_c, double* __restrict__ rd_c, Partial* __restrict__ partials) {
+  PdlScope pdl_scope;
   b_residual_restrict64(nf, phi, src, f, c, phi_c, phihat_c, rd_c, partials, blockIdx.x);
 }
 
@@ -68,6 +71,7 @@ __global__ void __launch_bounds__(256) k_residual_restrict64(
 __global__ void __launch_bounds__(256) k_finalize(const Partial* __restrict__ partials, int nparts,
                                                   double cells, int periodic,
                                                   LevelScalars* __restrict__ sc) {
+  PdlScope pdl_scope;
   b_finalize(partials, nparts, cells, periodic, sc, blockIdx.x);
 }
 
@@ -77,6 +81,7 @@ __global__ void __launch_bounds__(256) k_fas_rhs64(int nc, const double* __restr
                                                    double* __restrict__ f_c, OpConst64 c,
                                                    const LevelScalars* __restrict__ fine_sc,
                                                    LevelScalars* __restrict__ coarse_sc) {
+  PdlScope pdl_scope;
   b_fas_rhs64(nc, phi_c, src_c, f_c, c, fine_sc, coarse_sc, blockIdx.x);
 }
 
@@ -85,6 +90,7 @@ __global__ void __launch_bounds__(256) k_fas_rhs64(int nc, const double* __restr
 __global__ void __launch_bounds__(256) k_prolong_correct64(int nc, const double* __restrict__ phi_c,
                                                            const double* __restrict__ phihat_c,
                                                            double* __restrict__ phi_f) {
+  PdlScope pdl_scope;
   b_prolong_correct64(nc, phi_c, phihat_c, phi_f, blockIdx.x);
 }
 
@@ -95,12 +101,14 @@ __global__ void __launch_bounds__(256) k_coarsest64(int n, double* __restrict__ 
                                                     const double* __restrict__ f, OpConst64 c,
                                                     LevelScalars* __restrict__ sc, int max_sweeps,
                                                     double drop, int check_every) {
+  PdlScope pdl_scope;
   b_coarsest64(n, phi, src, f, c, sc, max_sweeps, drop, check_every, blockIdx.x);
 }
 
 // coarse = mean of the 8 children.
 __global__ void __launch_bounds__(256) k_restrict64(int nc, const double* __restrict__ fine,
                                                     double* __restrict__ coarse) {
+  PdlScope pdl_scope;
   const int nf = nc << 1;
   const long long cells = (long long)nc * nc * nc;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -123,24 +131,28 @@ __global__ void __launch_bounds__(256) k_affine64(long long cells, const double*
                                                   double* __restrict__ out, double a, double b,
                                                   double c3, int floor,
                                                   unsigned long long* __restrict__ floored) {
+  PdlScope pdl_scope;
   b_affine64(cells, delta, out, a, b, c3, floor, floored, blockIdx.x);
 }
 
 // Partial sums of x (for the gauge fix).
 __global__ void __launch_bounds__(256) k_sum_partials(long long cells, const double* __restrict__ x,
                                                       Partial* __restrict__ partials) {
+  PdlScope pdl_scope;
   b_sum_partials(cells, x, partials, blockIdx.x);
 }
 
 // x -= mean (the mean sits in sc->lambda, computed by k_finalize).
 __global__ void __launch_bounds__(256) k_sub_mean(long long cells, double* __restrict__ x,
                                                   const LevelScalars* __restrict__ sc) {
+  PdlScope pdl_scope;
   b_sub_mean(cells, x, sc, blockIdx.x);
 }
 
 // g = -(1/2) grad phi, central differences; out is 3 x n^3 (x, y, z).
 __global__ void __launch_bounds__(256) k_force64(int n, const double* __restrict__ phi,
                                                  double* __restrict__ out) {
+  PdlScope pdl_scope;
   const long long cells = (long long)n * n * n;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cells) return;
@@ -208,7 +220,7 @@ void launch_smooth64(cudaStream_t st, int n, double* phi, const double* src, con
   for (int s = 0; s < sweeps; ++s)
     for (int colour = 0; colour < 4; ++colour) {
       if (timer) timer->begin(st);
-      k_smooth_colour64<<<blocks_for(per, 256), 256, 0, st>>>(n, phi, src, f, sc, c, colour);
+      launch_k(k_smooth_colour64, blocks_for(per, 256), 256, 0, st, n, phi, src, f, sc, c, colour);
       if (timer) timer->end(st);
     }
   count_launches(4LL * sweeps);
@@ -221,8 +233,8 @@ void launch_residual64(cudaStream_t st, int n, const double* phi, const double* 
                        LevelScalars* sc, int periodic) {
   const long long cells = (long long)n * n * n;
   const unsigned nb = blocks_for(cells, 256);
-  k_residual64<<<nb, 256, 0, st>>>(n, phi, src, f, dout, c, partials);
-  k_finalize<<<1, 256, 0, st>>>(partials, (int)nb, (double)cells, periodic, sc);
+  launch_k(k_residual64, nb, 256, 0, st, n, phi, src, f, dout, c, partials);
+  launch_k(k_finalize, 1, 256, 0, st, partials, (int)nb, (double)cells, periodic, sc);
   count_launches(2);
 }
 
@@ -232,8 +244,8 @@ void launch_residual_restrict64(cudaStream_t st, int nf, const double* phi, cons
                                 LevelScalars* sc) {
   const long long ccells = (long long)(nf / 2) * (nf / 2) * (nf / 2);
   const unsigned nb = blocks_for(ccells, 256);
-  k_residual_restrict64<<<nb, 256, 0, st>>>(nf, phi, src, f, c, phi_c, phihat_c, rd_c, partials);
-  k_finalize<<<1, 256, 0, st>>>(partials, (int)nb, (double)nf * nf * nf, 1, sc);
+  launch_k(k_residual_restrict64, nb, 256, 0, st, nf, phi, src, f, c, phi_c, phihat_c, rd_c, partials);
+  launch_k(k_finalize, 1, 256, 0, st, partials, (int)nb, (double)nf * nf * nf, 1, sc);
   count_launches(2);
 }
 
@@ -241,7 +253,7 @@ void launch_fas_rhs64(cudaStream_t st, int nc, const double* phi_c, const double
                       double* f_c, const OpConst64& c, const LevelScalars* fine_sc,
                       LevelScalars* coarse_sc) {
   const long long cells = (long long)nc * nc * nc;
-  k_fas_rhs64<<<blocks_for(cells, 256), 256, 0, st>>>(nc, phi_c, src_c, f_c, c, fine_sc,
+  launch_k(k_fas_rhs64, blocks_for(cells, 256), 256, 0, st, nc, phi_c, src_c, f_c, c, fine_sc,
                                                       coarse_sc);
   count_launches(1);
 }
@@ -249,7 +261,7 @@ void launch_fas_rhs64(cudaStream_t st, int nc, const double* phi_c, const double
 void launch_prolong_correct64(cudaStream_t st, int nc, const double* phi_c,
                               const double* phihat_c, double* phi_f) {
   const long long cells = 8LL * nc * nc * nc;
-  k_prolong_correct64<<<blocks_for(cells, 256), 256, 0, st>>>(nc, phi_c, phihat_c, phi_f);
+  launch_k(k_prolong_correct64, blocks_for(cells, 256), 256, 0, st, nc, phi_c, phihat_c, phi_f);
   count_launches(1);
 }
 
@@ -262,34 +274,34 @@ void launch_coarsest64(cudaStream_t st, int n, double* phi, const double* src, c
                          3 * sizeof(double) * 4096);
     attr_set = true;
   }
-  k_coarsest64<<<1, 256, smem, st>>>(n, phi, src, f, c, sc, max_sweeps, drop, 2);
+  launch_k(k_coarsest64, 1, 256, smem, st, n, phi, src, f, c, sc, max_sweeps, drop, 2);
   count_launches(1);
 }
 
 void launch_restrict64(cudaStream_t st, int nc, const double* fine, double* coarse) {
   const long long cells = (long long)nc * nc * nc;
-  k_restrict64<<<blocks_for(cells, 256), 256, 0, st>>>(nc, fine, coarse);
+  launch_k(k_restrict64, blocks_for(cells, 256), 256, 0, st, nc, fine, coarse);
   count_launches(1);
 }
 
 void launch_affine64(cudaStream_t st, long long cells, const double* x, double* out, double a,
                      double b, double c3, int floor, unsigned long long* floored) {
-  k_affine64<<<blocks_for(cells, 256), 256, 0, st>>>(cells, x, out, a, b, c3, floor, floored);
+  launch_k(k_affine64, blocks_for(cells, 256), 256, 0, st, cells, x, out, a, b, c3, floor, floored);
   count_launches(1);
 }
 
 void launch_gauge64(cudaStream_t st, long long cells, double* x, Partial* partials,
                     LevelScalars* sc) {
   const unsigned nb = blocks_for(cells, 256);
-  k_sum_partials<<<nb, 256, 0, st>>>(cells, x, partials);
-  k_finalize<<<1, 256, 0, st>>>(partials, (int)nb, (double)cells, 1, sc);
-  k_sub_mean<<<nb, 256, 0, st>>>(cells, x, sc);
+  launch_k(k_sum_partials, nb, 256, 0, st, cells, x, partials);
+  launch_k(k_finalize, 1, 256, 0, st, partials, (int)nb, (double)cells, 1, sc);
+  launch_k(k_sub_mean, nb, 256, 0, st, cells, x, sc);
   count_launches(3);
 }
 
 void launch_force64(cudaStream_t st, int n, const double* phi, double* out) {
   const long long cells = (long long)n * n * n;
-  k_force64<<<blocks_for(cells, 256), 256, 0, st>>>(n, phi, out);
+  launch_k(k_force64, blocks_for(cells, 256), 256, 0, st, n, phi, out);
   count_launches(1);
 }
 
@@ -298,7 +310,7 @@ void launch_force64(cudaStream_t st, int n, const double* phi, double* out) {
 namespace mg {
 void launch_finalize(cudaStream_t st, const Partial* partials, int nparts, double cells,
                      int periodic, LevelScalars* sc) {
-  k_finalize<<<1, 256, 0, st>>>(partials, nparts, cells, periodic, sc);
+  launch_k(k_finalize, 1, 256, 0, st, partials, nparts, cells, periodic, sc);
   count_launches(1);
 }
 }  // namespace mg

@@ -12,6 +12,25 @@ namespace mg {
 
 void set_error(const std::string& msg);
 
+// Launch `k` on `st` with programmatic stream serialisation allowed: the kernel
+// may be scheduled while its predecessor in the stream finishes.  Every kernel
+// launched this way opens a PdlScope before touching memory.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                            cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(block, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // Kernel launches issued by this thread (graph captures included).
 extern thread_local long long tl_launches;
 inline void count_launches(long long k) { tl_launches += k; }

@@ -42,12 +42,14 @@ __global__ void __launch_bounds__(256) k_residual_handoff64(
     int n, const double* __restrict__ phi, const double* __restrict__ src, OpConst64 c,
     const LevelScalars* __restrict__ sc, float* __restrict__ g, float* __restrict__ q0,
     float* __restrict__ phi0, float* __restrict__ e, Partial* __restrict__ partials) {
+  PdlScope pdl_scope;
   b_residual_handoff64(n, phi, src, c, sc, g, q0, phi0, e, partials, blockIdx.x);
 }
 
 // phi += e (FP64).
 __global__ void __launch_bounds__(256) k_update64(long long cells, double* __restrict__ phi,
                                                   const float* __restrict__ e) {
+  PdlScope pdl_scope;
   b_update64(cells, phi, e, blockIdx.x);
 }
 
@@ -56,6 +58,7 @@ __global__ void __launch_bounds__(256) k_update64(long long cells, double* __res
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_restrict32(int nc, const float* __restrict__ fine,
                                                     float* __restrict__ coarse) {
+  PdlScope pdl_scope;
   b_restrict32(nc, fine, coarse, blockIdx.x);
 }
 
@@ -65,6 +68,7 @@ __global__ void __launch_bounds__(256) k_q0_prep32(int n, const float* __restric
                                                    const double* __restrict__ delta,
                                                    OpConst32 c, float kappa, int floor,
                                                    float* __restrict__ q0) {
+  PdlScope pdl_scope;
   b_q0_prep32(n, phi0, delta, c, kappa, floor, q0, blockIdx.x);
 }
 
@@ -74,6 +78,7 @@ __global__ void __launch_bounds__(256) k_smooth_colour32(int n, float* __restric
                                                          const float* __restrict__ g,
                                                          const LevelScalars* __restrict__ sc,
                                                          OpConst32 c, int colour) {
+  PdlScope pdl_scope;
   b_smooth_colour32(n, e, phi0, q0, g, sc, c, colour, blockIdx.x);
 }
 
@@ -83,6 +88,7 @@ __global__ void __launch_bounds__(256) k_residual_restrict32(
     const float* __restrict__ q0, const float* __restrict__ g, OpConst32 c,
     float* __restrict__ e_c, float* __restrict__ ehat_c, float* __restrict__ rg_c,
     Partial* __restrict__ partials) {
+  PdlScope pdl_scope;
   b_residual_restrict32(nf, e, phi0, q0, g, c, e_c, ehat_c, rg_c, partials, blockIdx.x);
 }
 
@@ -93,12 +99,14 @@ __global__ void __launch_bounds__(256) k_fas_rhs32(int nc, const float* __restri
                                                    float* __restrict__ g_c, OpConst32 c,
                                                    const LevelScalars* __restrict__ fine_sc,
                                                    LevelScalars* __restrict__ coarse_sc) {
+  PdlScope pdl_scope;
   b_fas_rhs32(nc, e_c, phi0_c, q0_c, g_c, c, fine_sc, coarse_sc, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_prolong_correct32(int nc, const float* __restrict__ e_c,
                                                            const float* __restrict__ ehat_c,
                                                            float* __restrict__ e_f) {
+  PdlScope pdl_scope;
   b_prolong_correct32(nc, e_c, ehat_c, e_f, blockIdx.x);
 }
 
@@ -110,6 +118,7 @@ __global__ void __launch_bounds__(256) k_coarsest_corr64(int n, float* __restric
                                                          const float* __restrict__ g, OpConst32 c,
                                                          LevelScalars* __restrict__ sc,
                                                          int max_sweeps, double drop) {
+  PdlScope pdl_scope;
   b_coarsest_corr64(n, e, phi0, q0, g, c, sc, max_sweeps, drop, blockIdx.x);
 }
 
@@ -216,7 +225,7 @@ struct CycleMixed {
     const long long per = (long long)(L.n / 2) * (L.n / 2) * L.n;
     for (int s = 0; s < sweeps; ++s)
       for (int colour = 0; colour < 4; ++colour)
-        k_smooth_colour32<<<nblk(per, 256), 256, 0, st>>>(L.n, L.e, L.phi0, L.q0, L.rhs, sc32(l),
+        launch_k(k_smooth_colour32, nblk(per, 256), 256, 0, st, L.n, L.e, L.phi0, L.q0, L.rhs, sc32(l),
                                                          ops32[l], colour);
     count_launches(4LL * sweeps);
   }
@@ -245,7 +254,7 @@ struct CycleMixed {
     }
     if (l == d->nlev - 1) {
       const size_t smem = 4 * sizeof(double) * (size_t)L.cells;
-      k_coarsest_corr64<<<1, 256, smem, st>>>(L.n, L.e, L.phi0, L.q0, L.rhs, ops32[l], sc32(l),
+      launch_k(k_coarsest_corr64, 1, 256, smem, st, L.n, L.e, L.phi0, L.q0, L.rhs, ops32[l], sc32(l),
                                               o->coarse_sweeps, o->coarse_drop);
       count_launches(1);
       return;
@@ -253,13 +262,13 @@ struct CycleMixed {
     Level& C = d->lv[l + 1];
     smooth(l, o->nu_pre);
     const unsigned nb = nblk(C.cells, 256);
-    k_residual_restrict32<<<nb, 256, 0, st>>>(L.n, L.e, L.phi0, L.q0, L.rhs, ops32[l], C.e,
+    launch_k(k_residual_restrict32, nb, 256, 0, st, L.n, L.e, L.phi0, L.q0, L.rhs, ops32[l], C.e,
                                                C.ehat, C.rhs, d->d_part);
     launch_finalize(st, d->d_part, (int)nb, (double)L.cells, 1, sc32(l));
-    k_fas_rhs32<<<nblk(C.cells, 256), 256, 0, st>>>(C.n, C.e, C.phi0, C.q0, C.rhs, ops32[l + 1],
+    launch_k(k_fas_rhs32, nblk(C.cells, 256), 256, 0, st, C.n, C.e, C.phi0, C.q0, C.rhs, ops32[l + 1],
                                                      sc32(l), sc32(l + 1));
     inner(l + 1);
-    k_prolong_correct32<<<nblk(L.cells, 256), 256, 0, st>>>(C.n, C.e, C.ehat, L.e);
+    launch_k(k_prolong_correct32, nblk(L.cells, 256), 256, 0, st, C.n, C.e, C.ehat, L.e);
     count_launches(3);  // residual-restrict, FAS right-hand side, prolongation
     smooth(l, o->nu_post);
   }
@@ -268,7 +277,7 @@ struct CycleMixed {
   void part_a() const {
     Level& L = d->lv[0];
     const unsigned nb = nblk(L.cells, 256);
-    k_residual_handoff64<<<nb, 256, 0, st>>>(L.n, L.phi, L.src, ops[0], d->d_sc, L.rhs, L.q0,
+    launch_k(k_residual_handoff64, nb, 256, 0, st, L.n, L.phi, L.src, ops[0], d->d_sc, L.rhs, L.q0,
                                               L.phi0, L.e, d->d_part);
     count_launches(1);
     launch_finalize(st, d->d_part, (int)nb, (double)L.cells, 1, d->d_sc);
@@ -279,15 +288,15 @@ struct CycleMixed {
   void part_b() const {
     for (int l = 1; l < d->nlev; ++l) {
       Level& L = d->lv[l];
-      k_restrict32<<<nblk(L.cells, 256), 256, 0, st>>>(L.n, d->lv[l - 1].phi0, L.phi0);
-      k_q0_prep32<<<nblk(L.cells, 256), 256, 0, st>>>(L.n, L.phi0, L.delta, ops32[l], kappa, floor,
+      launch_k(k_restrict32, nblk(L.cells, 256), 256, 0, st, L.n, d->lv[l - 1].phi0, L.phi0);
+      launch_k(k_q0_prep32, nblk(L.cells, 256), 256, 0, st, L.n, L.phi0, L.delta, ops32[l], kappa, floor,
                                                       L.q0);
       count_launches(2);
     }
     cudaMemsetAsync(sc32(0), 0, sizeof(LevelScalars), st);
     for (int c = 0; c < o->inner_cycles; ++c) inner(0);
     Level& L = d->lv[0];
-    k_update64<<<nblk(L.cells, 256), 256, 0, st>>>(L.cells, L.phi, L.e);
+    launch_k(k_update64, nblk(L.cells, 256), 256, 0, st, L.cells, L.phi, L.e);
     count_launches(1);
   }
 };

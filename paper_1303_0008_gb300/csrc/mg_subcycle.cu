@@ -24,6 +24,7 @@ namespace mg {
 __device__ __forceinline__ long long nblk256(long long work) { return (work + 255) / 256; }
 
 __global__ void __launch_bounds__(256) k_subcycle64(const __grid_constant__ SubCycleArgs a) {
+  PdlScope pdl_scope;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks();
   auto smooth = [&](const SubLevel64& L, int sweeps) {
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(256) k_subcycle64(const __grid_constant__ SubC
 }
 
 __global__ void __launch_bounds__(256) k_subcycle32(const __grid_constant__ SubCycleArgs a) {
+  PdlScope pdl_scope;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks();
   auto smooth = [&](const SubLevel32& L, int sweeps) {
@@ -146,13 +148,15 @@ static void launch_cluster(K kernel, cudaStream_t st, const SubCycleArgs& a, siz
   cfg.blockDim = dim3(256, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at;
-  at.id = cudaLaunchAttributeClusterDimension;
-  at.val.clusterDim.x = ctas;
-  at.val.clusterDim.y = 1;
-  at.val.clusterDim.z = 1;
-  cfg.attrs = &at;
-  cfg.numAttrs = 1;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = ctas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
   cudaLaunchKernelEx(&cfg, kernel, a);
   count_launches(1);
 }

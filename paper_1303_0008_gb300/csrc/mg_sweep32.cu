@@ -340,6 +340,7 @@ __device__ __forceinline__ void sweep_item(const Sweep32Args& A, float* ring, in
 }
 
 __global__ void __launch_bounds__(sw::THREADS, 2) k_sweep32(const __grid_constant__ Sweep32Args A) {
+  PdlScope pdl_scope;
   extern __shared__ __align__(16) float sm[];
   int* const xw = reinterpret_cast<int*>(sm + 2 * sw::RING * sw::SLOT);
   int* const yw = xw + sw::WX;
@@ -408,7 +409,7 @@ void launch_sweep32(cudaStream_t st, int n, const float* e_in, float* e_out, con
   a.c = c;
   const long long items = (long long)a.tiles_x * a.tiles_y * a.chunks;
   const int grid = (int)(items < 2LL * g_sweep_sms ? items : 2LL * g_sweep_sms);
-  k_sweep32<<<grid, sw::THREADS, sw::SMEM, st>>>(a);
+  launch_k(k_sweep32, grid, sw::THREADS, sw::SMEM, st, a);
   count_launches(1);
 }
 
