@@ -113,6 +113,11 @@ typedef struct {
                         levels with n >= 32, n % 4 == 0 as two one-launch four-colour
                         sweeps (same arithmetic, same bits as the per-colour launches);
                         0 keeps four launches per sweep (default). */
+  int pair32;        /* mixed precision: 1 updates two cells of a row per thread in the
+                        per-colour FP32 stages of levels with n % 4 == 0 (same bits as one
+                        cell per thread); 0 one cell per thread (default: the paired loads
+                        touch each sector twice and the stage is load-bound, so pairs
+                        measured 5-9 % slower per solve). */
 } mg_options;
 
 typedef struct {

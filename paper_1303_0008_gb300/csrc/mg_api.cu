@@ -63,6 +63,7 @@ void mg_default_options(mg_options* opt) {
   opt->patch_mg_levels = 3;
   opt->patch_cgc = 1.0;
   opt->sweep32 = 0;
+  opt->pair32 = 0;
 }
 
 static mg_status check_options(const mg_options& o) {
@@ -84,6 +85,7 @@ static mg_status check_options(const mg_options& o) {
   if (o.patch_mg_levels < 1 || o.patch_mg_levels > 3) MG_FAIL(MG_EINVAL, "options: patch_mg_levels");
   if (!(o.patch_cgc > 0.0 && o.patch_cgc <= 1.0)) MG_FAIL(MG_EINVAL, "options: patch_cgc");
   if (o.sweep32 != 0 && o.sweep32 != 1) MG_FAIL(MG_EINVAL, "options: sweep32");
+  if (o.pair32 != 0 && o.pair32 != 1) MG_FAIL(MG_EINVAL, "options: pair32");
   return MG_OK;
 }
 

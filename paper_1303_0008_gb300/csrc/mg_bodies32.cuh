@@ -75,6 +75,41 @@ __device__ __forceinline__ float gs_value32(const StencilT<float>& se, float dd,
                    1.f / 6.f);
 }
 
+// Two cells of one colour per thread (packed FP32x2 arithmetic, lane x = the
+// first cell, lane y = the second): the same operations lane by lane as the
+// scalar forms above, so the same bits.
+__device__ __forceinline__ float2 ld2(const float* p) {
+  return *reinterpret_cast<const float2*>(p);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b, rounded once: fma(b, -1, a) is the IEEE difference
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+
+struct Stencil2 {
+  float2 sx, sy, sz, cxy, cxz, cyz;
+};
+
+// dD32 on two cells at once (same operations, lane by lane).
+__device__ __forceinline__ float2 dD2(const Stencil2& se, const Stencil2& sp, float2 q0,
+                                      const OpConst32& c) {
+  const float2 two = splat(2.f);
+  const float2 a1e = sub2(se.sx, se.sy), a2e = sub2(se.sx, se.sz), a3e = sub2(se.sy, se.sz);
+  const float2 a1p = sub2(sp.sx, sp.sy), a2p = sub2(sp.sx, sp.sz), a3p = sub2(sp.sy, sp.sz);
+  const float2 dA = fma2(a3e, fma2(two, a3p, a3e),
+                         fma2(a2e, fma2(two, a2p, a2e), mul2(a1e, fma2(two, a1p, a1e))));
+  const float2 dB = fma2(se.cyz, fma2(two, sp.cyz, se.cyz),
+                         fma2(se.cxz, fma2(two, sp.cxz, se.cxz),
+                              mul2(se.cxy, fma2(two, sp.cxy, se.cxy))));
+  const float2 du = fma2(splat(c.g2), dB, mul2(splat(c.g1), dA));
+  const float2 q1 = fma2(splat(c.c3), du, q0);
+  return make_float2(root_change32(q0.x, q1.x, du.x, c), root_change32(q0.y, q1.y, du.y, c));
+}
+
 __device__ __forceinline__ void b_residual_handoff64(
     int n, const double* __restrict__ phi, const double* __restrict__ src, OpConst64 c,
     const LevelScalars* __restrict__ sc, float* __restrict__ g, float* __restrict__ q0,
@@ -188,6 +223,81 @@ __device__ __forceinline__ void b_smooth_colour32(int n, float* __restrict__ e,
   float dd = 0.f;
   if (!c.linear) dd = dD32(se, gather_at(phi0 + id, o), q0[id], c);
   e[id] = gs_value32(se, dd, g[id], s_mu, c);
+}
+
+// The colour stage of b_smooth_colour32 with two cells per thread: the cells
+// x and x + 2 of one row and colour (n % 4 == 0).  They share the x + 1 column of
+// their stencils, the second cell's loads sit 8 bytes past the first's, and the
+// arithmetic runs on both in the two lanes of packed FP32x2 instructions, each
+// lane doing exactly what b_smooth_colour32 does for its cell.
+__device__ __forceinline__ void b_smooth_colour32_pair(int n, float* __restrict__ e,
+                                                       const float* __restrict__ phi0,
+                                                       const float* __restrict__ q0,
+                                                       const float* __restrict__ g,
+                                                       const LevelScalars* __restrict__ sc,
+                                                       OpConst32 c, int colour, long long blk) {
+  __shared__ float s_mu;
+  if (threadIdx.x == 0) s_mu = (float)sc->lambda;
+  __syncthreads();
+  const int hn = n >> 1, qn = n >> 2;
+  const long long t = (long long)blk * blockDim.x + threadIdx.x;
+  if (t >= (long long)qn * hn * n) return;
+  // t -> (p, jj, k): p = t % qn, jj = (t / qn) % hn, k = t / (qn hn)
+  const unsigned ut = (unsigned)t, uq = (unsigned)qn, uh = (unsigned)hn;
+  int p, jj, k;
+  if (((uq & (uq - 1u)) | (uh & (uh - 1u))) == 0u) {
+    const unsigned rest = ut >> (__ffs(qn) - 1);
+    p = (int)(ut & (uq - 1u));
+    jj = (int)(rest & (uh - 1u));
+    k = (int)(rest >> (__ffs(hn) - 1));
+  } else {
+    const unsigned rest = ut / uq;
+    p = (int)(ut - rest * uq);
+    jj = (int)(rest % uh);
+    k = (int)(rest / uh);
+  }
+  const int i = 4 * p + ((colour ^ k) & 1);
+  const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
+  const long long id = lidx(i, j, k, n);
+  const NbrOff o = nbr_offsets(i, j, k, n);
+  const int xmA = o.xm;                        // -1, or n - 1 at i == 0
+  const int xpB = (i + 3 == n) ? 3 - n : 3;   // x + 1 of the second cell, from the first
+  // offsets (y, z part) of the 13 rows of the stencil
+  const int y0 = 0, yp = o.yp, ym = o.ym, zp = o.zp, zm = o.zm;
+  auto gather = [&](const float* __restrict__ b) {
+    Stencil2 st;
+    auto xrow = [&](int yz, float2& xpv, float2& xmv) {
+      const float sh = b[yz + 1];  // x + 1 of the first cell = x - 1 of the second
+      xpv = make_float2(sh, b[yz + xpB]);
+      xmv = make_float2(b[yz + xmA], sh);
+    };
+    auto col = [&](int yz) { return make_float2(b[yz], b[yz + 2]); };
+    float2 xp_, xm_, xpyp, xmyp, xpym, xmym, xpzp, xmzp, xpzm, xmzm;
+    xrow(y0, xp_, xm_);
+    xrow(yp, xpyp, xmyp);
+    xrow(ym, xpym, xmym);
+    xrow(zp, xpzp, xmzp);
+    xrow(zm, xpzm, xmzm);
+    const float2 ypv = col(yp), ymv = col(ym), zpv = col(zp), zmv = col(zm);
+    const float2 ypzp = col(yp + zp), ymzm = col(ym + zm), ypzm = col(yp + zm), ymzp = col(ym + zp);
+    st.sx = add2(xp_, xm_);
+    st.sy = add2(ypv, ymv);
+    st.sz = add2(zpv, zmv);
+    st.cxy = sub2(add2(xpyp, xmym), add2(xpym, xmyp));
+    st.cxz = sub2(add2(xpzp, xmzm), add2(xpzm, xmzp));
+    st.cyz = sub2(add2(ypzp, ymzm), add2(ypzm, ymzp));
+    return st;
+  };
+  float* const ea = e + id;
+  const Stencil2 ee = gather(ea);
+  float2 dd = make_float2(0.f, 0.f);
+  if (!c.linear) dd = dD2(ee, gather(phi0 + id), make_float2(q0[id], q0[id + 2]), c);
+  const float2 gv = make_float2(g[id], g[id + 2]);
+  const float2 v = mul2(fma2(splat(-c.h2), add2(dd, add2(gv, splat(s_mu))),
+                             add2(add2(ee.sx, ee.sy), ee.sz)),
+                        splat(1.f / 6.f));
+  ea[0] = v.x;
+  ea[2] = v.y;
 }
 
 __device__ __forceinline__ void b_residual_restrict32(

@@ -74,22 +74,6 @@ __device__ __forceinline__ int pmod(int v, int n) {
 __device__ __forceinline__ int wrap1(int k, int n) { return k < 0 ? k + n : (k >= n ? k - n : k); }
 __device__ __forceinline__ int slot_of(int k) { return (k + 8 * sw::RING) & (sw::RING - 1); }
 
-__device__ __forceinline__ float2 ld2(const float* p) {
-  return *reinterpret_cast<const float2*>(p);
-}
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-// a - b, rounded once: fma(b, -1, a) is the IEEE difference
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
-}
-__device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
-
-struct Stencil2 {
-  float2 sx, sy, sz, cxy, cxz, cyz;
-};
-
 // x neighbours of a cell pair from the other-parity half row at p (the pair at
 // the same index) and its aligned neighbour pair on the side the pair needs.
 template <int A>
@@ -130,22 +114,6 @@ __device__ __forceinline__ Stencil2 gather2(const float* Xm, const float* X0, co
   s.cxz = sub2(add2(xpzp, xmzm), add2(xpzm, xmzp));
   s.cyz = sub2(add2(ypzp, ymzm), add2(ypzm, ymzp));
   return s;
-}
-
-// dD32 on two cells at once (same operations, lane by lane).
-__device__ __forceinline__ float2 dD2(const Stencil2& se, const Stencil2& sp, float2 q0,
-                                      const OpConst32& c) {
-  const float2 two = splat(2.f);
-  const float2 a1e = sub2(se.sx, se.sy), a2e = sub2(se.sx, se.sz), a3e = sub2(se.sy, se.sz);
-  const float2 a1p = sub2(sp.sx, sp.sy), a2p = sub2(sp.sx, sp.sz), a3p = sub2(sp.sy, sp.sz);
-  const float2 dA = fma2(a3e, fma2(two, a3p, a3e),
-                         fma2(a2e, fma2(two, a2p, a2e), mul2(a1e, fma2(two, a1p, a1e))));
-  const float2 dB = fma2(se.cyz, fma2(two, sp.cyz, se.cyz),
-                         fma2(se.cxz, fma2(two, sp.cxz, se.cxz),
-                              mul2(se.cxy, fma2(two, sp.cxy, se.cxy))));
-  const float2 du = fma2(splat(c.g2), dB, mul2(splat(c.g1), dA));
-  const float2 q1 = fma2(splat(c.c3), du, q0);
-  return make_float2(root_change32(q0.x, q1.x, du.x, c), root_change32(q0.y, q1.y, du.y, c));
 }
 
 // Window row of this thread's cell pair for colour stage S on a plane whose

@@ -38,7 +38,7 @@ class mg_options(ctypes.Structure):
                 ("patch_coarse_sweeps", ctypes.c_int), ("fuse_coarse", ctypes.c_int),
                 ("omega", ctypes.c_double), ("omega_patch", ctypes.c_double),
                 ("patch_mg_levels", ctypes.c_int), ("patch_cgc", ctypes.c_double),
-                ("sweep32", ctypes.c_int)]
+                ("sweep32", ctypes.c_int), ("pair32", ctypes.c_int)]
 
 
 class mg_solve_stats(ctypes.Structure):

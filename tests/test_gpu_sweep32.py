@@ -1,4 +1,4 @@
-"""The one-launch four-colour FP32 sweep (z-marching wavefront, packed FP32x2
+"""The one-launch four-colour FP32 sweep and the two-cells-per-thread colour stage (z-marching wavefront, packed FP32x2
 arithmetic) against the per-colour launches: the same cell updates in the same
 order with the same roundings, so mixed-precision solves must agree bit for
 bit, histories included.  Sizes cover ragged 64 x 16 tiles (n = 40, 96), grids
@@ -72,3 +72,16 @@ def test_sweep32_solution_against_oracle():
 def test_sweep32_option_is_validated():
     with pytest.raises(mg.MGError):
         mg.mg_create_grid(32, mg.options(sweep32=2))
+
+
+@pytest.mark.parametrize("n,rv,sign", [(32, 8.0, 1.0), (40, 4.0, -1.0), (96, 8.0, -1.0),
+                                       (128, 32.0, 1.0), (64, 0.0, 1.0)])
+def test_pair32_matches_one_cell_per_thread_bitwise(n, rv, sign):
+    """Two cells of a row per thread (packed FP32x2) against one cell per thread."""
+    delta = I.lognormal_delta(n, 1.5, 700 + n)
+    alpha = sign * I.alpha_kappa_for_rv(rv) if rv > 0 else 0.0
+    st1, phi1 = mixed_solve(delta, alpha, sign, 1e-10, pair32=1)
+    st0, phi0 = mixed_solve(delta, alpha, sign, 1e-10, pair32=0)
+    assert st0["rc"] == mg.MG_OK and st1["rc"] == mg.MG_OK
+    assert st1["hist"] == st0["hist"]
+    assert np.array_equal(phi1, phi0)
