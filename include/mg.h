@@ -118,6 +118,10 @@ typedef struct {
                         cell per thread); 0 one cell per thread (default: the paired loads
                         touch each sector twice and the stage is load-bound, so pairs
                         measured 5-9 % slower per solve). */
+  double tau_stop;   /* FP64 domain solves: > 0 also stops once max|d - lambda| <=
+                        tau_stop * max|tau - mean tau|, tau = L^H(R phi) - R L^h(phi) the
+                        truncation-error estimate of Sec. III.C (the paper's criterion
+                        |d^h| <~ alpha |tau^h| with alpha <= 1/3); 0 (default) uses tol only */
 } mg_options;
 
 typedef struct {
@@ -137,6 +141,8 @@ typedef struct {
   long long kernel_launches; /* finest-level smoother launches timed (time_kernels) */
   double kernel_ms;    /* their summed device time in milliseconds */
   double kernel_cells; /* cell updates those launches performed */
+  double tau;          /* with tau_stop > 0: max |tau - mean tau| of the truncation-error
+                          estimate at the last check (FP64 domain solves), else 0 */
 } mg_solve_stats;
 
 /* Fill `opt` with the defaults listed above. */
@@ -235,6 +241,33 @@ void mg_destroy_grid(mg_grid* g);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* mg_last_error(void);
+
+/*
+ * Newtonian potential and total force (Sec. II.B, Eq. newton and the sentence
+ * after it).  mg_solve_newton solves the Poisson equation
+ *     (phi_N(i+1) + phi_N(i-1) + ... - 6 phi_N(i)) / h^2 = coef * delta,
+ * coef = (3/2) Omega_m a in code units, on the domain and on every refinement
+ * level of the handle, with the same FAS V-cycles as mg_solve in their linear
+ * (alpha = 0) form, into buffers of its own: the scalar field of mg_solve is
+ * left untouched, and phi_N persists between calls as the next initial guess.
+ * Refinement levels take their Dirichlet shells from phi_N of the level below.
+ * `stats` (nullable) describes the domain solve.  Errors as mg_solve, plus
+ * MG_EINVAL for a batch handle or a non-finite coef.
+ */
+mg_status mg_solve_newton(mg_grid* g, double coef, double tol, mg_solve_stats* stats);
+
+/* phi_N of (level, patch), addressed as in mg_get_field.  MG_ESTATE before the
+ * first mg_solve_newton. */
+mg_status mg_get_newton_field(const mg_grid* g, int level, int patch, double* out, int on_device);
+
+/*
+ * Total force -grad Psi with Psi = phi_N + phi / 2, the potential under which
+ * particles move in the DGP model: -grad phi_N plus the fifth force of
+ * mg_get_force, by the same central differences (evaluated as -1/2 grad of
+ * phi + 2 phi_N, including the refinement levels' ghost shells).  Layout and
+ * addressing as mg_get_force.  MG_ESTATE before the first mg_solve_newton.
+ */
+mg_status mg_get_total_force(const mg_grid* g, int level, int patch, double* out, int on_device);
 
 /*
  * Batched independent periodic solves (one handle, `count` grids of sides n[s],

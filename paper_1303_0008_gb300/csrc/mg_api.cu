@@ -64,6 +64,7 @@ void mg_default_options(mg_options* opt) {
   opt->patch_cgc = 1.0;
   opt->sweep32 = 0;
   opt->pair32 = 0;
+  opt->tau_stop = 0.0;
 }
 
 static mg_status check_options(const mg_options& o) {
@@ -86,6 +87,7 @@ static mg_status check_options(const mg_options& o) {
   if (!(o.patch_cgc > 0.0 && o.patch_cgc <= 1.0)) MG_FAIL(MG_EINVAL, "options: patch_cgc");
   if (o.sweep32 != 0 && o.sweep32 != 1) MG_FAIL(MG_EINVAL, "options: sweep32");
   if (o.pair32 != 0 && o.pair32 != 1) MG_FAIL(MG_EINVAL, "options: pair32");
+  if (!(o.tau_stop >= 0.0 && o.tau_stop < 1e3)) MG_FAIL(MG_EINVAL, "options: tau_stop");
   return MG_OK;
 }
 
@@ -162,6 +164,8 @@ void mg_destroy_grid(mg_grid* g) {
   for (auto& pl : g->patch_levels) patch_level_destroy(pl);
   batch_release(g);
   if (g->force_tmp) cudaFree(g->force_tmp);
+  for (auto* v : {&g->nw_phi, &g->nw_ghost, &g->nw_psi, &g->nw_psi_ghost})
+    for (double* p : *v) cudaFree(p);
   if (g->own_stream) cudaStreamDestroy(g->own_stream);
   delete g;
 }
@@ -483,6 +487,136 @@ mg_status mg_op_force(int n, const double* phi, double* out, void* stream) {
   launch_force64((cudaStream_t)stream, n, phi, out);
   MG_CK(cudaGetLastError());
   return MG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Newtonian potential (Eq. newton) and total force -grad(phi_N + phi / 2)
+// ---------------------------------------------------------------------------
+namespace {
+
+void free_vec(std::vector<double*>& v) {
+  for (double* p : v) cudaFree(p);
+  v.clear();
+}
+
+// phi_N buffers (zeroed when first made or when the patch layout changed) and
+// the scratch of the total force, one entry per level.
+mg_status ensure_newton(mg_grid* g) {
+  const size_t nl = 1 + g->patch_levels.size();
+  std::vector<size_t> cells(nl, 0), ghosts(nl, 0);
+  cells[0] = (size_t)g->domains[0]->lv[0].cells;
+  for (size_t l = 1; l < nl; ++l) {
+    const PatchLevel* pl = g->patch_levels[l - 1];
+    cells[l] = pl ? (size_t)pl->count * 512 : 0;
+    ghosts[l] = pl ? (size_t)pl->count * 1000 : 0;
+  }
+  if (cells == g->nw_cells && ghosts == g->nw_ghost_cells) return MG_OK;
+  for (auto* v : {&g->nw_phi, &g->nw_ghost, &g->nw_psi, &g->nw_psi_ghost}) free_vec(*v);
+  g->newton_set = false;
+  g->nw_cells.clear();
+  g->nw_ghost_cells.clear();
+  for (size_t l = 0; l < nl; ++l) {
+    double *a = nullptr, *b = nullptr, *c = nullptr, *e = nullptr;
+    bool ok = true;
+    if (cells[l]) {
+      ok = ok && cudaMalloc(&a, sizeof(double) * cells[l]) == cudaSuccess;
+      ok = ok && cudaMalloc(&c, sizeof(double) * cells[l]) == cudaSuccess;
+      if (ok) cudaMemsetAsync(a, 0, sizeof(double) * cells[l], g->stream);
+    }
+    if (ghosts[l]) {
+      ok = ok && cudaMalloc(&b, sizeof(double) * ghosts[l]) == cudaSuccess;
+      ok = ok && cudaMalloc(&e, sizeof(double) * ghosts[l]) == cudaSuccess;
+      if (ok) cudaMemsetAsync(b, 0, sizeof(double) * ghosts[l], g->stream);
+    }
+    g->nw_phi.push_back(a);
+    g->nw_psi.push_back(c);
+    g->nw_ghost.push_back(b);
+    g->nw_psi_ghost.push_back(e);
+    if (!ok) {
+      for (auto* v : {&g->nw_phi, &g->nw_ghost, &g->nw_psi, &g->nw_psi_ghost}) free_vec(*v);
+      MG_FAIL(MG_ENOMEM, "mg_solve_newton: device allocation");
+    }
+  }
+  g->nw_cells = cells;
+  g->nw_ghost_cells = ghosts;
+  return MG_OK;
+}
+
+// Exchange the solver's field (and ghost) buffers of every level with `phi`
+// (and `ghost`); applying it twice restores the handle.
+void swap_fields(mg_grid* g, std::vector<double*>& phi, std::vector<double*>& ghost) {
+  std::swap(g->domains[0]->lv[0].phi, phi[0]);
+  for (size_t l = 1; l < phi.size(); ++l) {
+    PatchLevel* pl = g->patch_levels[l - 1];
+    if (!pl || pl->count == 0) continue;
+    std::swap(pl->phi, phi[l]);
+    std::swap(pl->ghost, ghost[l]);
+  }
+}
+
+}  // namespace
+
+mg_status mg_solve_newton(mg_grid* g, double coef, double tol, mg_solve_stats* stats) {
+  if (!g || g->batch) MG_FAIL(MG_EINVAL, "mg_solve_newton: needs a domain handle");
+  if (!std::isfinite(coef) || !(tol > 0.0)) MG_FAIL(MG_EINVAL, "mg_solve_newton: coef/tol");
+  Domain* d = g->domains[0];
+  if (!d->density_set) MG_FAIL(MG_ESTATE, "mg_solve_newton: density not set");
+  for (PatchLevel* pl : g->patch_levels)
+    if (pl && pl->count && !pl->density_set)
+      MG_FAIL(MG_ESTATE, "mg_solve_newton: patch density not set");
+  mg_status st = ensure_newton(g);
+  if (st != MG_OK) return st;
+  mg_solve_stats local;
+  mg_solve_stats* s = stats ? stats : &local;
+  swap_fields(g, g->nw_phi, g->nw_ghost);
+  st = domain_solve(d, g->opt, g->stream, 0, 0.0, coef, tol, s);
+  for (size_t l = 0; st == MG_OK && l < g->patch_levels.size(); ++l) {
+    PatchLevel* pl = g->patch_levels[l];
+    if (!pl || pl->count == 0) continue;
+    st = patch_level_solve(g, (int)l + 1, 0, 0.0, coef, tol);
+  }
+  swap_fields(g, g->nw_phi, g->nw_ghost);
+  if (st == MG_OK) g->newton_set = true;
+  return st;
+}
+
+mg_status mg_get_newton_field(const mg_grid* g_const, int level, int patch, double* out,
+                              int on_device) {
+  mg_grid* g = const_cast<mg_grid*>(g_const);
+  if (!g || g->batch) MG_FAIL(MG_EINVAL, "mg_get_newton_field: needs a domain handle");
+  if (!g->newton_set || ensure_newton(g) != MG_OK || !g->newton_set)
+    MG_FAIL(MG_ESTATE, "mg_get_newton_field: no Newtonian solve yet");
+  swap_fields(g, g->nw_phi, g->nw_ghost);
+  const mg_status st = mg_get_field(g, level, patch, out, on_device);
+  swap_fields(g, g->nw_phi, g->nw_ghost);
+  return st;
+}
+
+mg_status mg_get_total_force(const mg_grid* g_const, int level, int patch, double* out,
+                             int on_device) {
+  mg_grid* g = const_cast<mg_grid*>(g_const);
+  if (!g || g->batch) MG_FAIL(MG_EINVAL, "mg_get_total_force: needs a domain handle");
+  if (!g->newton_set || ensure_newton(g) != MG_OK || !g->newton_set)
+    MG_FAIL(MG_ESTATE, "mg_get_total_force: no Newtonian solve yet");
+  if (level < 0 || level >= (int)g->nw_cells.size() || g->nw_cells[level] == 0)
+    MG_FAIL(MG_EINVAL, "mg_get_total_force: no such level");
+  // psi = phi + 2 phi_N (and the same for the ghost shells, which are linear in
+  // the fields), then the fifth-force stencil -1/2 grad psi
+  if (level == 0) {
+    launch_axpy64(g->stream, (long long)g->nw_cells[0], g->domains[0]->lv[0].phi, g->nw_phi[0],
+                  2.0, g->nw_psi[0]);
+  } else {
+    PatchLevel* pl = g->patch_levels[level - 1];
+    launch_axpy64(g->stream, (long long)g->nw_cells[level], pl->phi, g->nw_phi[level], 2.0,
+                  g->nw_psi[level]);
+    launch_axpy64(g->stream, (long long)g->nw_ghost_cells[level], pl->ghost,
+                  g->nw_ghost[level], 2.0, g->nw_psi_ghost[level]);
+  }
+  MG_CK(cudaGetLastError());
+  swap_fields(g, g->nw_psi, g->nw_psi_ghost);
+  const mg_status st = mg_get_force(g, level, patch, out, on_device);
+  swap_fields(g, g->nw_psi, g->nw_psi_ghost);
+  return st;
 }
 
 }  // extern "C"

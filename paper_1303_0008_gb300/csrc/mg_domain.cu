@@ -10,6 +10,7 @@
 // test: when max|d - lambda| < tol the cycle stops there, so every cycle costs
 // one finest-level residual.  The two halves of the cycle (up to that test,
 // and after it) are captured once per solve as CUDA graphs and replayed.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -186,12 +187,21 @@ struct Cycle64 {
     launch_residual_restrict64(st, L.n, L.phi, L.src, nullptr, ops[0], C.phi, C.phihat, C.f,
                                d->d_part, d->d_sc);
     cudaMemcpyAsync(d->h_sc, d->d_sc, sizeof(LevelScalars), cudaMemcpyDeviceToHost, st);
+    if (o->tau_stop > 0.0) {
+      // The first coarse FAS right-hand side is L^H(R phi) - R L^h(phi) + lambda^h, the
+      // truncation-error estimate (finest f = 0); its spread goes to the host too.
+      LevelScalars* tsc = d->d_sc + 2 * d->nlev;
+      launch_fas_rhs64(st, C.n, C.phi, C.src, C.f, ops[1], d->d_sc, d->d_sc + 1);
+      launch_spread64(st, C.cells, C.f, d->d_part, tsc);
+      cudaMemcpyAsync(d->h_sc + 1, tsc, sizeof(LevelScalars), cudaMemcpyDeviceToHost, st);
+    }
   }
 
   void part_b() const {
     Level& L = d->lv[0];
     Level& C = d->lv[1];
-    launch_fas_rhs64(st, C.n, C.phi, C.src, C.f, ops[1], d->d_sc, d->d_sc + 1);
+    if (!(o->tau_stop > 0.0))  // else part_a computed it
+      launch_fas_rhs64(st, C.n, C.phi, C.src, C.f, ops[1], d->d_sc, d->d_sc + 1);
     descend(1);
     launch_prolong_correct64(st, C.n, C.phi, C.phihat, L.phi);
     launch_smooth64(st, L.n, L.phi, L.src, nullptr, d->d_sc, ops[0], o->nu_post, timer_b);
@@ -333,6 +343,11 @@ mg_status domain_solve(Domain* d, const mg_options& o, cudaStream_t st, int bran
       s->guard_hits = o.guard == MG_GUARD_FLOOR ? (long long)d->h_sc[0].floored
                                                 : d->h_sc[0].guards;
       s->lambda = d->h_sc[0].lambda;
+      if (o.tau_stop > 0.0 && !single) {
+        // stop at a fraction of the truncation error as well (Sec. III.C)
+        s->tau = d->h_sc[1].res;
+        tr.tol = std::max(tol, o.tau_stop * s->tau);
+      }
       result = tr.step(d->h_sc[0].res, &done);
       if (done || result != MG_OK) break;
       if (!single) {

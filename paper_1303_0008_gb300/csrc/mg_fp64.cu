@@ -299,6 +299,31 @@ void launch_gauge64(cudaStream_t st, long long cells, double* x, Partial* partia
   count_launches(3);
 }
 
+// max |x - mean x| into sc->res (sc->lambda = mean x)
+void launch_spread64(cudaStream_t st, long long cells, const double* x, Partial* partials,
+                     LevelScalars* sc) {
+  const unsigned nb = blocks_for(cells, 256);
+  launch_k(k_sum_partials, nb, 256, 0, st, cells, x, partials);
+  launch_k(k_finalize, 1, 256, 0, st, partials, (int)nb, (double)cells, 1, sc);
+  count_launches(2);
+}
+
+// out = x + a y
+__global__ void __launch_bounds__(256) k_axpy64(long long cells, const double* __restrict__ x,
+                                                const double* __restrict__ y, double a,
+                                                double* __restrict__ out) {
+  PdlScope pdl_scope;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < cells) out[t] = fma(a, y[t], x[t]);
+}
+
+void launch_axpy64(cudaStream_t st, long long cells, const double* x, const double* y, double a,
+                   double* out) {
+  if (cells <= 0) return;
+  launch_k(k_axpy64, blocks_for(cells, 256), 256, 0, st, cells, x, y, a, out);
+  count_launches(1);
+}
+
 void launch_force64(cudaStream_t st, int n, const double* phi, double* out) {
   const long long cells = (long long)n * n * n;
   launch_k(k_force64, blocks_for(cells, 256), 256, 0, st, n, phi, out);

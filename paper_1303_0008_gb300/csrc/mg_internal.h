@@ -131,6 +131,10 @@ void launch_affine64(cudaStream_t st, long long cells, const double* x, double* 
 void launch_gauge64(cudaStream_t st, long long cells, double* x, Partial* partials,
                     LevelScalars* sc);
 void launch_force64(cudaStream_t st, int n, const double* phi, double* out);
+void launch_spread64(cudaStream_t st, long long cells, const double* x, Partial* partials,
+                     LevelScalars* sc);
+void launch_axpy64(cudaStream_t st, long long cells, const double* x, const double* y, double a,
+                   double* out);
 
 }  // namespace mg
 

@@ -91,6 +91,11 @@ struct mg_grid {
   std::vector<mg::PatchLevel*> patch_levels;
   double* force_tmp = nullptr;
   size_t force_tmp_bytes = 0;
+  // Newtonian potential: per level (0 = domain, l = refinement level l) phi_N, its
+  // ghost shells, and scratch for phi + 2 phi_N; element counts per level
+  std::vector<double*> nw_phi, nw_ghost, nw_psi, nw_psi_ghost;
+  std::vector<size_t> nw_cells, nw_ghost_cells;
+  bool newton_set = false;
   mg::BatchState* bs = nullptr;
 };
 

@@ -38,7 +38,8 @@ class mg_options(ctypes.Structure):
                 ("patch_coarse_sweeps", ctypes.c_int), ("fuse_coarse", ctypes.c_int),
                 ("omega", ctypes.c_double), ("omega_patch", ctypes.c_double),
                 ("patch_mg_levels", ctypes.c_int), ("patch_cgc", ctypes.c_double),
-                ("sweep32", ctypes.c_int), ("pair32", ctypes.c_int)]
+                ("sweep32", ctypes.c_int), ("pair32", ctypes.c_int),
+                ("tau_stop", ctypes.c_double)]
 
 
 class mg_solve_stats(ctypes.Structure):
@@ -48,7 +49,7 @@ class mg_solve_stats(ctypes.Structure):
                 ("guard_hits", ctypes.c_longlong), ("hist_len", ctypes.c_int),
                 ("res_hist", ctypes.c_double * 128), ("launches", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("kernel_ms", ctypes.c_double),
-                ("kernel_cells", ctypes.c_double)]
+                ("kernel_cells", ctypes.c_double), ("tau", ctypes.c_double)]
 
     def as_dict(self):
         return {"cycles": self.cycles, "outer": self.outer, "status": self.status,
@@ -56,7 +57,7 @@ class mg_solve_stats(ctypes.Structure):
                 "lambda": self.lambda_, "wall_s": self.wall_s, "guard_hits": self.guard_hits,
                 "hist": list(self.res_hist[:self.hist_len]), "launches": self.launches,
                 "kernel_launches": self.kernel_launches, "kernel_ms": self.kernel_ms,
-                "kernel_cells": self.kernel_cells}
+                "kernel_cells": self.kernel_cells, "tau": self.tau}
 
 
 _lib = None
@@ -75,6 +76,9 @@ _SIGS = {
     "mg_solve": (_I, [_P, _I, _F, _F, _F, ctypes.POINTER(mg_solve_stats)]),
     "mg_get_field": (_I, [_P, _I, _I, _P, _I]),
     "mg_get_force": (_I, [_P, _I, _I, _P, _I]),
+    "mg_solve_newton": (_I, [_P, _F, _F, ctypes.POINTER(mg_solve_stats)]),
+    "mg_get_newton_field": (_I, [_P, _I, _I, _P, _I]),
+    "mg_get_total_force": (_I, [_P, _I, _I, _P, _I]),
     "mg_destroy_grid": (None, [_P]),
     "mg_last_error": (ctypes.c_char_p, []),
     "mg_create_batch": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(ctypes.c_int),
@@ -237,6 +241,28 @@ def mg_get_field(g, level: int, patch: int, out):
 def mg_get_force(g, level: int, patch: int, out):
     p, dev, _ = _arr(out, writable=True)
     _check(lib().mg_get_force(g, level, patch, p, dev), "mg_get_force")
+    return out
+
+
+def mg_solve_newton(g, coef: float, tol: float, check: bool = True):
+    st = mg_solve_stats()
+    rc = lib().mg_solve_newton(g, coef, tol, ctypes.byref(st))
+    if check and rc != MG_OK:
+        raise MGError(rc, f"mg_solve_newton: {mg_last_error()}")
+    d = st.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def mg_get_newton_field(g, level: int, patch: int, out):
+    p, dev, _ = _arr(out, writable=True)
+    _check(lib().mg_get_newton_field(g, level, patch, p, dev), "mg_get_newton_field")
+    return out
+
+
+def mg_get_total_force(g, level: int, patch: int, out):
+    p, dev, _ = _arr(out, writable=True)
+    _check(lib().mg_get_total_force(g, level, patch, p, dev), "mg_get_total_force")
     return out
 
 
