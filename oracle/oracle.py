@@ -37,6 +37,8 @@ def lib():
         L.orc_residual.restype = ctypes.c_long
         L.orc_residual.argtypes = [ctypes.c_int, ctypes.c_double, _D, _D, _D, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_int, ctypes.c_double, _D]
+        L.orc_assign.restype = ctypes.c_int
+        L.orc_assign.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_long, _D, _D, _D, _D, _D]
         L.orc_density_floor.restype = ctypes.c_long
         L.orc_density_floor.argtypes = [ctypes.c_long, _D, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, _D]
@@ -197,3 +199,39 @@ def patch_ghosts(n0, level, org, parent, parent_org=None, fill=np.nan):
     if st != 0:
         raise ValueError("nesting violated: a ghost needs a parent cell outside the parent level")
     return out
+
+
+def assign_density(nside, pos, mass=None, scheme=2):
+    """Mass assignment (Sec. VI): rho on a periodic nside^3 cell-centred grid from
+    particles at pos (3, count) in box units; scheme 1 = CIC, 2 = TSC; masses in
+    units of the total mass (None: 1/count each).  Returns delta = rho - 1."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    count = pos.shape[1]
+    m = None if mass is None else _f64(mass)
+    rho = np.zeros((nside,) * 3)
+    rc = lib().orc_assign(nside, scheme, count, _p(pos[0]), _p(pos[1]), _p(pos[2]),
+                          None if m is None else _p(m), _p(rho))
+    if rc:
+        raise ValueError("scheme must be 1 (CIC) or 2 (TSC)")
+    return rho - 1.0
+
+
+def refine_blocks(delta, npc, particle_mass, covered=None):
+    """Refinement criterion (Sec. III.B: refine where the effective number of
+    particles in a cell exceeds N_pc), on 4^3-aligned blocks of a level of side
+    n: a block is refined when any of its cells holds more than npc effective
+    particles, (1 + delta) h^3 / particle_mass.  `covered` (bool, n^3) limits the
+    blocks to cells that exist on this level.  Returns the origins (x, y, z) of
+    the next level's 8^3 patches (twice the block origins), sorted by z, y, x."""
+    delta = np.asarray(delta, dtype=np.float64)
+    n = delta.shape[0]
+    count = (1.0 + delta) / float(n) ** 3 / particle_mass
+    hot = count > npc
+    if covered is not None:
+        hot &= covered
+    b = n // 4
+    blocks = hot.reshape(b, 4, b, 4, b, 4).any(axis=(1, 3, 5))  # [bz, by, bx]
+    bz, by, bx = np.nonzero(blocks)
+    org = np.stack([bx, by, bz], axis=1).astype(np.int32) * 8
+    order = np.lexsort((org[:, 0], org[:, 1], org[:, 2]))
+    return org[order]

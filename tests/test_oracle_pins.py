@@ -587,3 +587,71 @@ def test_floor_makes_the_strong_screening_case_converge():
     fl, hits = O.density_floor(delta, a, 1.0)
     _, st = O.fas_solve(fl, a, 1.0, tol=1e-10, max_cycles=60)
     assert st["status"] == O.OK and st["guard_hits"] == 0
+
+
+# ---------------------------------------------------------------------------
+# Mass assignment (Sec. VI) and the refinement criterion (Sec. III.B)
+# ---------------------------------------------------------------------------
+def _rand_particles(count, seed):
+    return np.random.default_rng(seed).random((3, count))
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_assignment_conserves_mass_and_maps_a_lattice_to_uniform_density(scheme):
+    n = 12
+    pos = _rand_particles(500, 3)
+    mass = np.random.default_rng(4).random(500)
+    mass /= mass.sum()
+    d = O.assign_density(n, pos, mass, scheme)
+    assert abs((d + 1.0).sum() / n ** 3 - 1.0) < 1e-14
+    # particles on the cell centres: the weights sum to one on every cell
+    g = (np.arange(n) + 0.5) / n
+    lat = np.stack([a.ravel() for a in np.meshgrid(g, g, g, indexing="ij")])
+    assert np.abs(O.assign_density(n, lat, None, scheme)).max() < 1e-13
+
+
+def test_tsc_is_cic_averaged_over_one_cell():
+    """TSC is the cloud-in-cell kernel convolved with a one-cell box: the TSC
+    density of a particle equals the mean of CIC densities of copies spread
+    uniformly over a cell around it (midpoint rule, error O(1/m^2))."""
+    n, m = 8, 24
+    x0 = np.array([3.3, 4.71, 2.05]) / n
+    t = ((np.arange(m) + 0.5) / m - 0.5) / n
+    sx, sy, sz = np.meshgrid(t, t, t, indexing="ij")
+    pos = np.stack([x0[0] + sx.ravel(), x0[1] + sy.ravel(), x0[2] + sz.ravel()])
+    cic = O.assign_density(n, pos, None, 1)
+    tsc = O.assign_density(n, x0.reshape(3, 1), None, 2)
+    assert np.abs((cic + 1) - (tsc + 1)).max() < 3.0 / m ** 2 * np.abs(tsc + 1).max()
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_assignment_is_periodic_and_translation_equivariant(scheme):
+    n = 10
+    pos = _rand_particles(200, 9)
+    d = O.assign_density(n, pos, None, scheme)
+    shifted = np.mod(pos + np.array([[3.0], [-1.0], [7.0]]) / n, 1.0)
+    d2 = O.assign_density(n, shifted, None, scheme)
+    assert np.abs(np.roll(d, (7, -1, 3), axis=(0, 1, 2)) - d2).max() < 1e-12
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_assignment_keeps_the_centre_of_mass(scheme):
+    n = 16
+    x = np.array([[0.41], [0.52], [0.37]])
+    rho = O.assign_density(n, x, None, scheme) + 1.0
+    c = (np.arange(n) + 0.5) / n
+    w = rho / rho.sum()
+    com = [(w * c[None, None, :]).sum(), (w * c[None, :, None]).sum(),
+           (w * c[:, None, None]).sum()]
+    assert np.allclose(com, x.ravel(), atol=1e-14)
+
+
+def test_refinement_blocks_hand_built():
+    n = 16
+    delta = np.zeros((n, n, n))
+    mp = 1.0 / n ** 3                       # one particle per cell on average
+    delta[9, 2, 13] = 9.5                   # 10.5 effective particles: refine
+    delta[0, 0, 0] = 7.9                    # 8.9 effective particles: not with npc = 9
+    org = O.refine_blocks(delta, 9.0, mp)
+    assert org.tolist() == [[24, 0, 16]]    # block (3, 0, 2) -> level-1 origin x2 x4
+    assert O.refine_blocks(delta, 8.0, mp).tolist() == [[0, 0, 0], [24, 0, 16]]
