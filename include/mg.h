@@ -201,6 +201,10 @@ mg_status mg_solve(mg_grid* g, int branch, double alpha, double kappa, double to
 /* Copy the field out (same addressing as mg_set_density). */
 mg_status mg_get_field(const mg_grid* g, int level, int patch, double* out, int on_device);
 
+/* The density contrast delta of (level, patch) as the solver holds it (after
+ * mg_set_density or mg_assign_density), addressed as in mg_get_field. */
+mg_status mg_get_density(const mg_grid* g, int level, int patch, double* out, int on_device);
+
 /*
  * The fifth force g = -(1/2) grad(phi) (Sec. II.B) by central differences
  * (Sec. III.B), as 3 x cells float64 (x components, then y, then z).  Level 0:
@@ -268,6 +272,40 @@ mg_status mg_get_newton_field(const mg_grid* g, int level, int patch, double* ou
  * addressing as mg_get_force.  MG_ESTATE before the first mg_solve_newton.
  */
 mg_status mg_get_total_force(const mg_grid* g, int level, int patch, double* out, int on_device);
+
+/*
+ * Particles to mesh (Sec. VI: the density on the mesh comes from assigning the
+ * particles with the triangular-shaped-cloud scheme).  Sets delta = rho - 1 on
+ * the domain (level 0, every cell) or on the patches of a refinement level
+ * (only cells inside a patch receive mass), then prepares it as mg_set_density.
+ *   scheme  MG_TSC (27 cells, W(u) = 3/4 - u^2 for |u| <= 1/2 and
+ *           (3/2 - |u|)^2 / 2 for 1/2 < |u| < 3/2) or MG_CIC (8 cells, 1 - |u|),
+ *           u the per-axis distance from a cell centre in cells
+ *   pos     3 x count doubles, SoA (all x, then all y, then all z), box units;
+ *           periodic (folded into [0, 1)); a non-finite coordinate drops the particle
+ *   mass    count doubles in units of the total mass of the box (mean density 1),
+ *           or NULL for 1/count each
+ * The FP64 atomic additions run in no fixed order: the last bits of a cell can
+ * vary between runs.  Errors: MG_EINVAL (batch handle, scheme, count <= 0, no
+ * patches on the level), MG_ENOMEM, MG_ECUDA.
+ */
+#define MG_CIC 1
+#define MG_TSC 2
+mg_status mg_assign_density(mg_grid* g, int level, int scheme, long long count, const double* pos,
+                            const double* mass, int on_device);
+
+/*
+ * Refinement criterion (Sec. III.B: refine a cell when the effective number of
+ * particles in it exceeds N_pc; Sec. V uses N_pc = 9): every 4^3-aligned block
+ * of `level` (the domain, or the blocks of that level's patches) holding a cell
+ * with (1 + delta) h^3 / particle_mass > npc becomes an 8^3 patch of level + 1,
+ * whose origin (twice the block origin) is written to `origins` (3 int32 each,
+ * sorted by z, then y, then x).  At most max_count origins are written; *found
+ * receives how many there are.  particle_mass is in units of the total mass
+ * (1/count for equal masses).  MG_ESTATE if the level has no density.
+ */
+mg_status mg_refine_blocks(const mg_grid* g, int level, double npc, double particle_mass,
+                           int32_t* origins, int max_count, int* found);
 
 /*
  * Batched independent periodic solves (one handle, `count` grids of sides n[s],

@@ -24,21 +24,6 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 
 using namespace mg;
 
-#define MG_CK(call)                                                                   \
-  do {                                                                                \
-    cudaError_t e_ = (call);                                                          \
-    if (e_ != cudaSuccess) {                                                          \
-      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
-      return MG_ECUDA;                                                                \
-    }                                                                                 \
-  } while (0)
-
-#define MG_FAIL(code, msg)  \
-  do {                      \
-    set_error(msg);         \
-    return code;            \
-  } while (0)
-
 extern "C" {
 
 const char* mg_last_error(void) { return g_last_error.c_str(); }
@@ -298,6 +283,15 @@ mg_status mg_get_field(const mg_grid* g, int level, int patch, double* out, int 
   double* src;
   size_t cnt;
   mg_status st = resolve(g, level, patch, true, &src, &cnt);
+  if (st != MG_OK) return st;
+  return copy_out(g, out, src, cnt, on_device);
+}
+
+mg_status mg_get_density(const mg_grid* g, int level, int patch, double* out, int on_device) {
+  if (!g) MG_FAIL(MG_EINVAL, "mg_get_density: NULL handle");
+  double* src;
+  size_t cnt;
+  mg_status st = resolve(g, level, patch, false, &src, &cnt);
   if (st != MG_OK) return st;
   return copy_out(g, out, src, cnt, on_device);
 }

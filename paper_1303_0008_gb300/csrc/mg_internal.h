@@ -12,6 +12,22 @@ namespace mg {
 
 void set_error(const std::string& msg);
 
+// Status returns of the C-ABI entry points.
+#define MG_CK(call)                                                                   \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+      return MG_ECUDA;                                                                \
+    }                                                                                 \
+  } while (0)
+
+#define MG_FAIL(code, msg)  \
+  do {                      \
+    set_error(msg);         \
+    return code;            \
+  } while (0)
+
 // Launch `k` on `st` with programmatic stream serialisation allowed: the kernel
 // may be scheduled while its predecessor in the stream finishes.  Every kernel
 // launched this way opens a PdlScope before touching memory.

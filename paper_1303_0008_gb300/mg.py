@@ -76,7 +76,11 @@ _SIGS = {
     "mg_solve": (_I, [_P, _I, _F, _F, _F, ctypes.POINTER(mg_solve_stats)]),
     "mg_get_field": (_I, [_P, _I, _I, _P, _I]),
     "mg_get_force": (_I, [_P, _I, _I, _P, _I]),
+    "mg_get_density": (_I, [_P, _I, _I, _P, _I]),
     "mg_solve_newton": (_I, [_P, _F, _F, ctypes.POINTER(mg_solve_stats)]),
+    "mg_assign_density": (_I, [_P, _I, _I, ctypes.c_longlong, _P, _P, _I]),
+    "mg_refine_blocks": (_I, [_P, _I, _F, _F, ctypes.POINTER(ctypes.c_int32), _I,
+                              ctypes.POINTER(ctypes.c_int)]),
     "mg_get_newton_field": (_I, [_P, _I, _I, _P, _I]),
     "mg_get_total_force": (_I, [_P, _I, _I, _P, _I]),
     "mg_destroy_grid": (None, [_P]),
@@ -238,6 +242,12 @@ def mg_get_field(g, level: int, patch: int, out):
     return out
 
 
+def mg_get_density(g, level: int, patch: int, out):
+    p, dev, _ = _arr(out, writable=True)
+    _check(lib().mg_get_density(g, level, patch, p, dev), "mg_get_density")
+    return out
+
+
 def mg_get_force(g, level: int, patch: int, out):
     p, dev, _ = _arr(out, writable=True)
     _check(lib().mg_get_force(g, level, patch, p, dev), "mg_get_force")
@@ -264,6 +274,31 @@ def mg_get_total_force(g, level: int, patch: int, out):
     p, dev, _ = _arr(out, writable=True)
     _check(lib().mg_get_total_force(g, level, patch, p, dev), "mg_get_total_force")
     return out
+
+
+MG_CIC, MG_TSC = 1, 2
+
+
+def mg_assign_density(g, level: int, pos, mass=None, scheme: int = MG_TSC):
+    """pos: (3, count) float64 (numpy or CUDA tensor, C-contiguous, box units)."""
+    p, dev, keep = _arr(pos)
+    count = (pos.shape[1] if len(pos.shape) == 2 else pos.shape[0] // 3)
+    mp, mdev, keep2 = (None, dev, None) if mass is None else _arr(mass)
+    if mass is not None and mdev != dev:
+        raise ValueError("pos and mass must both be host or both be device arrays")
+    _check(lib().mg_assign_density(g, level, scheme, count, p, mp, dev), "mg_assign_density")
+
+
+def mg_refine_blocks(g, level: int, npc: float, particle_mass: float):
+    """Origins (k, 3) int32 of the next level's patches (Sec. III.B criterion)."""
+    found = ctypes.c_int()
+    _check(lib().mg_refine_blocks(g, level, npc, particle_mass, None, 0, ctypes.byref(found)),
+           "mg_refine_blocks")
+    out = np.zeros((max(found.value, 1), 3), dtype=np.int32)
+    _check(lib().mg_refine_blocks(g, level, npc, particle_mass,
+                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  found.value, ctypes.byref(found)), "mg_refine_blocks")
+    return out[:found.value]
 
 
 def mg_get_level_stats(g, level):
