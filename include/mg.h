@@ -122,6 +122,11 @@ typedef struct {
                         tau_stop * max|tau - mean tau|, tau = L^H(R phi) - R L^h(phi) the
                         truncation-error estimate of Sec. III.C (the paper's criterion
                         |d^h| <~ alpha |tau^h| with alpha <= 1/3); 0 (default) uses tol only */
+  double w;          /* operator-splitting constant of Sigma (Sec. III.A; the paper takes
+                        1/3, the default).  Another value in [0, 1) makes Sigma depend on
+                        the cell's own value and each smoothing update a full Newton step
+                        with the Jacobian diagonal of Sec. III.B; FP64 domain solves only
+                        (MG_EINVAL with MG_MIXED, refinement levels or batches). */
 } mg_options;
 
 typedef struct {

@@ -50,6 +50,7 @@ void mg_default_options(mg_options* opt) {
   opt->sweep32 = 0;
   opt->pair32 = 0;
   opt->tau_stop = 0.0;
+  opt->w = 1.0 / 3.0;
 }
 
 static mg_status check_options(const mg_options& o) {
@@ -73,6 +74,7 @@ static mg_status check_options(const mg_options& o) {
   if (o.sweep32 != 0 && o.sweep32 != 1) MG_FAIL(MG_EINVAL, "options: sweep32");
   if (o.pair32 != 0 && o.pair32 != 1) MG_FAIL(MG_EINVAL, "options: pair32");
   if (!(o.tau_stop >= 0.0 && o.tau_stop < 1e3)) MG_FAIL(MG_EINVAL, "options: tau_stop");
+  if (!(o.w >= 0.0 && o.w < 1.0)) MG_FAIL(MG_EINVAL, "options: w");
   return MG_OK;
 }
 
@@ -352,6 +354,11 @@ mg_status mg_solve(mg_grid* g, int branch, double alpha, double kappa, double to
   if (!std::isfinite(kappa) || !(tol > 0.0)) MG_FAIL(MG_EINVAL, "mg_solve: kappa/tol");
   Domain* d = g->domains[0];
   if (!d->density_set) MG_FAIL(MG_ESTATE, "mg_solve: density not set");
+  if (g->opt.w != 1.0 / 3.0 && alpha != 0.0) {
+    if (g->opt.prec != MG_FP64) MG_FAIL(MG_EINVAL, "mg_solve: w != 1/3 needs MG_FP64");
+    for (PatchLevel* pl : g->patch_levels)
+      if (pl && pl->count) MG_FAIL(MG_EINVAL, "mg_solve: w != 1/3 on refinement levels");
+  }
   mg_solve_stats local;
   mg_solve_stats* s = stats ? stats : &local;
   st = domain_solve(d, g->opt, g->stream, branch, alpha, kappa, tol, s);
@@ -370,6 +377,7 @@ mg_status mg_solve_batch(mg_grid* g, const int* branch, const double* alpha, con
                          double tol, mg_solve_stats* stats) {
   if (!g || !g->batch) MG_FAIL(MG_EINVAL, "mg_solve_batch: needs a batch handle");
   if (!branch || !alpha || !kappa || !(tol > 0.0)) MG_FAIL(MG_EINVAL, "mg_solve_batch: arguments");
+  if (g->opt.w != 1.0 / 3.0) MG_FAIL(MG_EINVAL, "mg_solve_batch: w must be 1/3");
   for (size_t s = 0; s < g->domains.size(); ++s) {
     mg_status st = check_branch(branch[s], alpha[s]);
     if (st != MG_OK) return st;

@@ -459,7 +459,7 @@ void launch_gauge64(cudaStream_t st, long long cells, double* x, Partial* partia
                     LevelScalars* sc);
 mg_status domain_prepare_sources(Domain* d, cudaStream_t st, int branch, double alpha,
                                  double kappa, int guard, double omega,
-                                 std::vector<OpConst64>& ops);
+                                 std::vector<OpConst64>& ops, double w);
 OpConst32 make_op32(int n, double alpha, int branch);
 
 mg_status batch_solve(mg_grid* g, const int* branch, const double* alpha, const double* kappa,
@@ -498,7 +498,7 @@ mg_status batch_solve(mg_grid* g, const int* branch, const double* alpha, const 
     std::memset(&sv[s], 0, sizeof(mg_solve_stats));
     sv[s].levels = d->nlev;
     mg_status ps = domain_prepare_sources(d, st, branch[s], alpha[s], kappa[s], o.guard, o.omega,
-                                          P.ops[s]);
+                                          P.ops[s], 1.0 / 3.0);
     if (ps != MG_OK) return ps;
     P.kappa[s] = (float)kappa[s];
     if (mixed) {

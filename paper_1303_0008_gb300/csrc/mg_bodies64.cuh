@@ -18,7 +18,10 @@ __device__ __forceinline__ void b_smooth_colour64(int n, double* __restrict__ ph
   // D = k2s sqrt(q) - k2, so phi_new = upd_s sqrt(q) + (Sx+Sy+Sz)/6 - h^2 f/6 + C with
   // the block-wide C = -h^2 (lambda - k2)/6.
   __shared__ double s_c;
-  if (threadIdx.x == 0) s_c = -c.h2_6 * (c.mode == OP_SQRT ? sc->lambda - c.k2 : sc->lambda);
+  // (OP_GENW keeps lambda itself here: its update is the Newton step below)
+  if (threadIdx.x == 0)
+    s_c = c.mode == OP_GENW ? sc->lambda
+                            : -c.h2_6 * (c.mode == OP_SQRT ? sc->lambda - c.k2 : sc->lambda);
   __syncthreads();
   const int hn = n >> 1;
   const long long t = (long long)blk * blockDim.x + threadIdx.x;
@@ -30,6 +33,12 @@ __device__ __forceinline__ void b_smooth_colour64(int n, double* __restrict__ ph
   const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
   const long long id = lidx(i, j, k, n);
   const StencilT<double> s = gather_periodic(phi, i, j, k, n);
+  if (c.mode == OP_GENW) {
+    const double old = phi[id];
+    const double v = genw_newton(s, old, src[id], (f ? f[id] : 0.0) + s_c, c);
+    phi[id] = c.omega != 1.0 ? fma(c.omega, v - old, old) : v;
+    return;
+  }
   const double lapnb = s.sx + s.sy + s.sz;
   double acc = fma(lapnb, 1.0 / 6.0, s_c);
   if (f) acc = fma(f[id], -c.h2_6, acc);
@@ -69,8 +78,8 @@ __device__ __forceinline__ void b_residual_restrict64(
       const long long id = lidx(i, j, k, nf);
       const StencilT<double> s = gather_periodic(phi, i, j, k, nf);
       bool g;
-      const double D = root_D(s, src[id], c, g);
       const double ctr = phi[id];
+      const double D = root_Dc(s, ctr, src[id], c, g);
       const double lap = (s.sx + s.sy + s.sz) - 6.0 * ctr;
       double d = fma(lap, c.inv_h2, -D);
       if (f) d -= f[id];
@@ -120,7 +129,7 @@ __device__ __forceinline__ void b_fas_rhs64(int nc, const double* __restrict__ p
   split3((unsigned)t, nc, i, j, k);
   const StencilT<double> s = gather_periodic(phi_c, i, j, k, nc);
   bool g;
-  const double D = root_D(s, src_c[t], c, g);
+  const double D = root_Dc(s, phi_c[t], src_c[t], c, g);
   const double lap = (s.sx + s.sy + s.sz) - 6.0 * phi_c[t];
   const double L = fma(lap, c.inv_h2, -D);
   f_c[t] = L - f_c[t] + fine_sc->lambda;
@@ -177,7 +186,7 @@ __device__ __forceinline__ void b_coarsest64(int n, double* __restrict__ phi,
       const int i = q % n, j = (q / n) % n, k = q / (n * n);
       const StencilT<double> s = gather_periodic<double>(sphi, i, j, k, n);
       bool g;
-      const double D = root_D(s, ssrc[q], c, g);
+      const double D = root_Dc(s, sphi[q], ssrc[q], c, g);
       const double lnb = s.sx + s.sy + s.sz;
       const double lap = lnb - 6.0 * sphi[q];
       partial_add(p, fma(lap, c.inv_h2, -D) - sf[q], g);
@@ -211,9 +220,14 @@ __device__ __forceinline__ void b_coarsest64(int n, double* __restrict__ phi,
         const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
         const int id = i + n * (j + n * k);
         const StencilT<double> s = gather_periodic<double>(sphi, i, j, k, n);
-        bool g;
-        const double D = root_D(s, ssrc[id], c, g);
-        const double v = fma(-c.h2, D + sf[id] + s_lam, s.sx + s.sy + s.sz) * (1.0 / 6.0);
+        double v;
+        if (c.mode == OP_GENW) {
+          v = genw_newton(s, sphi[id], ssrc[id], sf[id] + s_lam, c);
+        } else {
+          bool g;
+          const double D = root_D(s, ssrc[id], c, g);
+          v = fma(-c.h2, D + sf[id] + s_lam, s.sx + s.sy + s.sz) * (1.0 / 6.0);
+        }
         sphi[id] = (c.omega != 1.0) ? fma(c.omega, v - sphi[id], sphi[id]) : v;
       }
       __syncthreads();

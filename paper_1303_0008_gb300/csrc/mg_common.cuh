@@ -26,7 +26,8 @@ namespace mg {
 enum OpMode : int {
   OP_LINEAR = 0,  // alpha == 0: D = kappa*delta
   OP_SQRT = 1,    // D = k2 (sigma sqrt(q) - 1); src = 1 + c3 kappa delta
-  OP_CONJ = 2     // physical root as 2u/(1+sqrt(q)) for small |alpha|; src = kappa delta
+  OP_CONJ = 2,    // physical root as 2u/(1+sqrt(q)) for small |alpha|; src = kappa delta
+  OP_GENW = 3     // splitting w != 1/3: Sigma involves the centre value (full Newton step)
 };
 
 // Per-level constants of the FP64 operator.
@@ -42,6 +43,10 @@ struct OpConst64 {
   double h2_6;      // h^2/6
   double upd_s;     // -h^2 k2s / 6: the smoother's coefficient of sqrt(q)
   double omega;     // relaxation of the pointwise Newton step (1 = the plain step)
+  // OP_GENW: q = src + gA (Dxx^2 + Dyy^2 + Dzz^2) + gB (Dxx Dyy + Dxx Dzz + Dyy Dzz)
+  //            + gC (Cxy^2 + Cxz^2 + Cyz^2), the D's including the centre value;
+  //          gAB = gA + gB, so dq/dphi_centre = -4 gAB (Sx + Sy + Sz - 6 phi)
+  double gA, gB, gC, gAB;
   int mode;
 };
 
@@ -189,6 +194,41 @@ __device__ __forceinline__ double root_D(const StencilT<double>& s, double src,
   guard = q < 0.0;
   if (guard) return -c.k2;
   return (2.0 * u) / (1.0 + sqrt(q));
+}
+
+// Discriminant of a cell for a general splitting constant w (Sec. III.B,
+// Sigma_ijk with every second difference taken through the centre value).
+__device__ __forceinline__ double genw_q(const StencilT<double>& s, double ctr, double src,
+                                         const OpConst64& c) {
+  const double dxx = fma(-2.0, ctr, s.sx), dyy = fma(-2.0, ctr, s.sy), dzz = fma(-2.0, ctr, s.sz);
+  const double sq = fma(dxx, dxx, fma(dyy, dyy, dzz * dzz));
+  const double cr = fma(dxx, dyy, fma(dxx, dzz, dyy * dzz));
+  const double cc = fma(s.cxy, s.cxy, fma(s.cxz, s.cxz, s.cyz * s.cyz));
+  return fma(c.gA, sq, fma(c.gB, cr, fma(c.gC, cc, src)));
+}
+
+// D of any mode; ctr (the cell's own value) enters only for OP_GENW.
+__device__ __forceinline__ double root_Dc(const StencilT<double>& s, double ctr, double src,
+                                          const OpConst64& c, bool& guard) {
+  if (c.mode != OP_GENW) return root_D(s, src, c, guard);
+  const double q = genw_q(s, ctr, src, c);
+  guard = q < 0.0;
+  return fma(c.k2s, sqrt_nonneg(guard ? 0.0 : q), -c.k2);
+}
+
+// Newton step of one cell for OP_GENW: phi - L/(dL/dphi) with
+// L = (Sx + Sy + Sz - 6 phi)/h^2 - D - rhs and dL/dphi = -6/h^2 - dD/dphi, where
+// dD/dphi = -2 k2s gAB (Sx + Sy + Sz - 6 phi) / sqrt(q) (taken as 0 for q <= 1e-12).
+__device__ __forceinline__ double genw_newton(const StencilT<double>& s, double ctr, double src,
+                                              double rhs, const OpConst64& c) {
+  const double q = genw_q(s, ctr, src, c);
+  const double sq = sqrt_nonneg(q < 0.0 ? 0.0 : q);
+  const double D = fma(c.k2s, sq, -c.k2);
+  const double lap6 = fma(-6.0, ctr, s.sx + s.sy + s.sz);
+  const double L = fma(lap6, c.inv_h2, -D) - rhs;
+  const double dD = q > 1e-12 ? -2.0 * c.k2s * c.gAB * lap6 / sq : 0.0;
+  const double J = fma(-6.0, c.inv_h2, -dD);
+  return ctr - L / J;
 }
 
 // Deterministic block reduction of (sum, max, min, guards, nonfinite).

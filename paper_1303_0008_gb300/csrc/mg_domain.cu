@@ -261,11 +261,11 @@ mg_status mixed_solve(Domain* d, const mg_options& o, cudaStream_t st, const OpC
 
 mg_status domain_prepare_sources(Domain* d, cudaStream_t st, int branch, double alpha,
                                  double kappa, int guard, double omega,
-                                 std::vector<OpConst64>& ops) {
+                                 std::vector<OpConst64>& ops, double w) {
   ops.resize(d->nlev);
   DCK(cudaMemsetAsync(d->d_sc, 0, sizeof(LevelScalars) * (2 * d->nlev + 2), st));
   for (int l = 0; l < d->nlev; ++l) {
-    ops[l] = make_op64(d->lv[l].n, alpha, kappa, branch);
+    ops[l] = make_op64(d->lv[l].n, alpha, kappa, branch, w);
     ops[l].omega = omega;
     double a, b;
     src_coefficients(ops[l], kappa, &a, &b);
@@ -283,7 +283,7 @@ mg_status domain_solve(Domain* d, const mg_options& o, cudaStream_t st, int bran
   s->levels = d->nlev;
   const long long launches0 = tl_launches;
   std::vector<OpConst64> ops;
-  mg_status rs = domain_prepare_sources(d, st, branch, alpha, kappa, o.guard, o.omega, ops);
+  mg_status rs = domain_prepare_sources(d, st, branch, alpha, kappa, o.guard, o.omega, ops, o.w);
   if (rs != MG_OK) return rs;
   cudaEvent_t e0, e1;
   DCK(cudaEventCreate(&e0));

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) k_residual64(int n, const double* __restr
     const int k = (int)(t / ((long long)n * n));
     const StencilT<double> s = gather_periodic(phi, i, j, k, n);
     bool g;
-    const double D = root_D(s, src[t], c, g);
+    const double D = root_Dc(s, phi[t], src[t], c, g);
     const double lap = (s.sx + s.sy + s.sz) - 6.0 * phi[t];
     double d = fma(lap, c.inv_h2, -D);
     if (f) d -= f[t];
@@ -172,10 +172,9 @@ static inline unsigned blocks_for(long long work, int threads) {
   return (unsigned)((work + threads - 1) / threads);
 }
 
-OpConst64 make_op64(int n, double alpha, double kappa, int branch) {
+OpConst64 make_op64(int n, double alpha, double kappa, int branch, double w) {
   OpConst64 c{};
   const double h = 1.0 / (double)n;
-  const double w = 1.0 / 3.0;
   c.h2 = h * h;
   c.inv_h2 = (double)n * (double)n;
   c.h2_6 = c.h2 / 6.0;
@@ -199,11 +198,19 @@ OpConst64 make_op64(int n, double alpha, double kappa, int branch) {
   // k2 (sigma sqrt(q) - 1) loses about |k2| * eps to cancellation on the physical
   // root; below |alpha| = 1e-4 the conjugate form 2u/(1+sqrt q) is used instead.
   c.mode = (sigma > 0 && fabs(alpha) < 1e-4) ? OP_CONJ : OP_SQRT;
+  if (w != 1.0 / 3.0) {
+    // Sec. III.B with a general splitting constant: q = src + c3 alpha Sigma_ijk
+    c.mode = OP_GENW;
+    c.gA = c.c3 * alpha * (1.0 - w) / h4;
+    c.gB = -2.0 * c.c3 * alpha * w / h4;
+    c.gC = c.c3 * alpha / (8.0 * h4);
+    c.gAB = c.gA + c.gB;
+  }
   return c;
 }
 
 void src_coefficients(const OpConst64& c, double kappa, double* a, double* b) {
-  if (c.mode == OP_SQRT) {
+  if (c.mode == OP_SQRT || c.mode == OP_GENW) {
     *a = c.c3 * kappa;
     *b = 1.0;
   } else {

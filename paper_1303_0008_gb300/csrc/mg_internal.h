@@ -118,7 +118,7 @@ inline cudaGraphExec_t capture_graph(cudaStream_t st, long long* launches, const
 }
 
 // ---- FP64 periodic kernels (mg_fp64.cu) ----
-OpConst64 make_op64(int n, double alpha, double kappa, int branch);
+OpConst64 make_op64(int n, double alpha, double kappa, int branch, double w = 1.0 / 3.0);
 void src_coefficients(const OpConst64& c, double kappa, double* a, double* b);
 int partials_needed(long long cells);
 void launch_smooth64(cudaStream_t st, int n, double* phi, const double* src, const double* f,

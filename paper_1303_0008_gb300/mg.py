@@ -39,7 +39,7 @@ class mg_options(ctypes.Structure):
                 ("omega", ctypes.c_double), ("omega_patch", ctypes.c_double),
                 ("patch_mg_levels", ctypes.c_int), ("patch_cgc", ctypes.c_double),
                 ("sweep32", ctypes.c_int), ("pair32", ctypes.c_int),
-                ("tau_stop", ctypes.c_double)]
+                ("tau_stop", ctypes.c_double), ("w", ctypes.c_double)]
 
 
 class mg_solve_stats(ctypes.Structure):

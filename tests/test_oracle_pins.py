@@ -655,3 +655,24 @@ def test_refinement_blocks_hand_built():
     org = O.refine_blocks(delta, 9.0, mp)
     assert org.tolist() == [[24, 0, 16]]    # block (3, 0, 2) -> level-1 origin x2 x4
     assert O.refine_blocks(delta, 8.0, mp).tolist() == [[0, 0, 0], [24, 0, 16]]
+
+
+@pytest.mark.parametrize("w", [0.2, 1.0 / 3.0, 0.5])
+def test_general_w_solution_satisfies_the_unsplit_equation(w):
+    """For any splitting constant w the split root of Eq. two_branch, with the
+    periodic compatibility constant lambda (D = lap - lambda), is equivalent to
+    the unsplit discrete equation with a known lambda term:
+      lap + a [lap^2 - tr H^2] = kappa delta + lambda + a (1 - w) lambda (2 lap - lambda),
+    H the discrete Hessian of Sec. III.B (computed here independently)."""
+    n = 16
+    h = 1.0 / n
+    rng = np.random.default_rng(90)
+    delta = rng.uniform(-0.8, 0.8, size=(n, n, n))
+    delta -= delta.mean()
+    alpha, kappa = 0.3, 1.0
+    phi, st = O.fas_solve(delta, alpha, kappa, tol=1e-13, max_cycles=200, w=w)
+    assert st["status"] == O.OK and st["guard_hits"] == 0
+    lhs, lap, _ = unsplit_lhs(phi, h, alpha)
+    lam = st["lambda"]
+    rhs = kappa * delta + lam + alpha * (1 - w) * lam * (2 * lap - lam)
+    assert np.abs(lhs - rhs).max() < 1e-9 * np.abs(kappa * delta).max()
