@@ -86,13 +86,16 @@ def _pi(a):
     return None if a is None else a.ctypes.data_as(_I32)
 
 
-def residual(phi, delta, alpha, kappa, branch=0, f=None, w=W_PAPER):
-    """d = L^h phi - f on a periodic grid; returns (d, guarded cells)."""
+def residual(phi, delta, alpha, kappa, branch=0, f=None, w=W_PAPER, h=None):
+    """d = L^h phi - f on a periodic grid; returns (d, guarded cells).  h defaults
+    to 1/n; passing the spacing of a larger grid evaluates a cell of that grid from
+    its 3^3 neighbourhood (the centre of a 3^3 array)."""
     phi, delta = _f64(phi), _f64(delta)
     n = phi.shape[0]
     f = None if f is None else _f64(f)
     d = np.empty_like(phi)
-    g = lib().orc_residual(n, 1.0 / n, _p(phi), _p(delta), _p(f), alpha, kappa, branch, w, _p(d))
+    g = lib().orc_residual(n, 1.0 / n if h is None else h, _p(phi), _p(delta), _p(f), alpha,
+                           kappa, branch, w, _p(d))
     return d, int(g)
 
 

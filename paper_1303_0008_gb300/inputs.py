@@ -59,6 +59,32 @@ def gaussian_field(n: int, seed: int, spectral_index: float = -2.0) -> np.ndarra
     return g
 
 
+def lognormal_delta_device(n: int, sigma: float, seed: int, device="cuda"):
+    """The lognormal recipe of lognormal_delta drawn with torch on `device` (for
+    grids whose host FFT would be slow); its own random stream, float64."""
+    import torch
+    gen = torch.Generator(device=device).manual_seed(seed)
+    white = torch.randn((n, n, n), generator=gen, dtype=torch.float64, device=device)
+    wk = torch.fft.rfftn(white)
+    del white
+    f = torch.fft.fftfreq(n, device=device, dtype=torch.float64) * n
+    fr = torch.fft.rfftfreq(n, device=device, dtype=torch.float64) * n
+    k2 = (2.0 * math.pi) ** 2 * (f[:, None, None] ** 2 + f[None, :, None] ** 2 +
+                                 fr[None, None, :] ** 2)
+    amp = torch.where(k2 > 0, k2.clamp_min(1e-300) ** (-0.5), torch.zeros_like(k2))
+    del k2
+    wk *= amp
+    del amp
+    g = torch.fft.irfftn(wk, s=(n, n, n))
+    del wk
+    g -= g.mean()
+    g /= g.std()
+    rho = torch.exp(sigma * g - 0.5 * sigma * sigma)
+    del g
+    rho /= rho.mean()
+    return rho - 1.0
+
+
 def lognormal_delta(n: int, sigma: float, seed: int) -> np.ndarray:
     """delta = rho - 1 with rho = exp(sigma g - sigma^2/2) renormalised to mean 1."""
     g = sigma * gaussian_field(n, seed)

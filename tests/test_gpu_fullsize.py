@@ -88,3 +88,37 @@ def test_c4_512_mixed_and_fp64():
     # the mixed answer is the FP64 system's solution to the bound of the target
     assert rel(out[1][1], out[0][1]) < 1e-7
     assert rel(O.force(out[1][1]), O.force(out[0][1])) < 1e-7
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_largest_grid_1024_sampled_residual(prec):
+    """n = 1024, the largest grid the library accepts (2^30 cells per array):
+    a lognormal field drawn on the device, solved to 1e-8; the oracle evaluates
+    the operator at 2048 sampled cells from their 3^3 neighbourhoods."""
+    n = 1024
+    delta = I.lognormal_delta_device(n, 1.0, 1306)
+    alpha = I.alpha_kappa_for_rv(8.0)
+    g = mg.mg_create_grid(n, mg.options(prec=prec))
+    try:
+        mg.mg_set_density(g, 0, -1, delta)
+        st = mg.mg_solve(g, 0, alpha, 1.0, TOL)
+        phi = torch.empty_like(delta)
+        mg.mg_get_field(g, 0, -1, phi)
+    finally:
+        mg.mg_destroy_grid(g)
+    assert st["rc"] == mg.MG_OK and st["res"] < TOL and st["guard_hits"] == 0
+    rng = np.random.default_rng(1024 + prec)
+    c = torch.from_numpy(rng.integers(0, n, size=(2048, 3))).cuda()
+    o = torch.arange(-1, 2, device="cuda")
+    K = (c[:, 2, None, None, None] + o[None, :, None, None]) % n
+    J = (c[:, 1, None, None, None] + o[None, None, :, None]) % n
+    Ii = (c[:, 0, None, None, None] + o[None, None, None, :]) % n
+    pb = phi[K, J, Ii].cpu().numpy()
+    db = delta[K, J, Ii].cpu().numpy()
+    del phi, delta
+    worst = 0.0
+    for s in range(pb.shape[0]):
+        d, gh = O.residual(pb[s], db[s], alpha, 1.0, h=1.0 / n)
+        assert gh == 0
+        worst = max(worst, abs(d[1, 1, 1] - st["lambda"]))
+    assert worst <= st["res"] * (1 + 1e-6) + 1e-12
