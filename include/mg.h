@@ -32,9 +32,9 @@
  *     periodic box, and the constant lambda (reported in the statistics) takes up
  *     the difference.  The residual reported and tested against `tol` is
  *     max |d - lambda|, d = L^h phi.
- *   - The square root of Eq. two_branch is taken of max(q, 0): where the
- *     discriminant is negative the root is its real part, and the cell is counted
- *     in guard_hits.
+ *   - Where the discriminant of Eq. two_branch could turn negative, mg_guard
+ *     (below) selects the reading: by default the source is held at the bound
+ *     that keeps every root real; the cells concerned are counted in guard_hits.
  */
 #ifndef MG_H
 #define MG_H

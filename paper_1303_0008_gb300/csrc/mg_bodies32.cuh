@@ -6,32 +6,26 @@
 
 namespace mg {
 
-// sqrt and division of the correction operator: correctly rounded in FP64 (the
-// coarsest inner level), the fast hardware forms in FP32 (the correction only has
-// to be accurate to FP32 precision).
-__device__ __forceinline__ double root_of(double q) { return sqrt(q); }
-__device__ __forceinline__ float root_of(float q) { return q > 0.f ? q * rsqrtf(q) : 0.f; }
-__device__ __forceinline__ double ratio_of(double a, double b) { return a / b; }
-__device__ __forceinline__ float ratio_of(float a, float b) { return __fdividef(a, b); }
-
-// The change of the root D when phi0 moves by e, from the stencils of e and phi0.
-template <typename T>
-__device__ __forceinline__ T delta_D(const StencilT<T>& se, const StencilT<T>& sp, T q0, T g1,
-                                     T g2, T c3, T k2, T sigma, T& du_out) {
-  const T a1e = se.sx - se.sy, a2e = se.sx - se.sz, a3e = se.sy - se.sz;
-  const T a1p = sp.sx - sp.sy, a2p = sp.sx - sp.sz, a3p = sp.sy - sp.sz;
-  const T two = T(2);
-  const T dA = a1e * (two * a1p + a1e) + a2e * (two * a2p + a2e) + a3e * (two * a3p + a3e);
-  const T dB = se.cxy * (two * sp.cxy + se.cxy) + se.cxz * (two * sp.cxz + se.cxz) +
-               se.cyz * (two * sp.cyz + se.cyz);
-  const T du = g1 * dA + g2 * dB;
-  du_out = du;
-  const T q1 = q0 + c3 * du;
-  const T s0 = root_of(q0 > T(0) ? q0 : T(0));
-  const T s1 = root_of(q1 > T(0) ? q1 : T(0));
-  if (q0 >= T(0) && q1 >= T(0)) {
-    const T den = s0 + s1;
-    return den > T(0) ? ratio_of(sigma * two * du, den) : T(0);
+// The change of the root D when phi0 moves by e, from the stencils of e and
+// phi0, in FP64 with correctly rounded sqrt and division (the coarsest level of
+// the inner correction cycles): D(q1) - D(q0) = 2 sigma du / (sqrt q0 + sqrt q1)
+// where both discriminants are non-negative, k2 sigma (sqrt q1 - sqrt q0) of the
+// guarded roots otherwise.
+__device__ __forceinline__ double delta_D64(const StencilT<double>& se,
+                                            const StencilT<double>& sp, double q0, double g1,
+                                            double g2, double c3, double k2, double sigma) {
+  const double a1e = se.sx - se.sy, a2e = se.sx - se.sz, a3e = se.sy - se.sz;
+  const double a1p = sp.sx - sp.sy, a2p = sp.sx - sp.sz, a3p = sp.sy - sp.sz;
+  const double dA = a1e * (2.0 * a1p + a1e) + a2e * (2.0 * a2p + a2e) + a3e * (2.0 * a3p + a3e);
+  const double dB = se.cxy * (2.0 * sp.cxy + se.cxy) + se.cxz * (2.0 * sp.cxz + se.cxz) +
+                    se.cyz * (2.0 * sp.cyz + se.cyz);
+  const double du = g1 * dA + g2 * dB;
+  const double q1 = q0 + c3 * du;
+  const double s0 = sqrt(q0 > 0.0 ? q0 : 0.0);
+  const double s1 = sqrt(q1 > 0.0 ? q1 : 0.0);
+  if (q0 >= 0.0 && q1 >= 0.0) {
+    const double den = s0 + s1;
+    return den > 0.0 ? (sigma * 2.0 * du) / den : 0.0;
   }
   return sigma * k2 * (s1 - s0);
 }
@@ -414,8 +408,7 @@ __device__ __forceinline__ void b_coarsest_corr64(int n, float* __restrict__ e,
                sigma = (double)c.sigma;
   auto ddv = [&](const StencilT<double>& a, const StencilT<double>& b, double qq) {
     if (c.linear) return 0.0;
-    double du;
-    return delta_D<double>(a, b, qq, g1, g2, c3, k2, sigma, du);
+    return delta_D64(a, b, qq, g1, g2, c3, k2, sigma);
   };
   double scale = 0.0;
   auto residual = [&]() {

@@ -113,32 +113,10 @@ __global__ void __launch_bounds__(256) k_subcycle32(const __grid_constant__ SubC
   }
 }
 
-// Cluster size for a kernel: 16 CTAs where the device runs a non-portable
-// cluster of that size, else the portable 8.
-template <typename K>
-static int cluster_size(K kernel) {
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return 8;
-  }
-  cudaLaunchConfig_t probe = {};
-  probe.gridDim = dim3(16, 1, 1);
-  probe.blockDim = dim3(256, 1, 1);
-  probe.dynamicSmemBytes = 4 * sizeof(double) * 4096;
-  cudaLaunchAttribute at;
-  at.id = cudaLaunchAttributeClusterDimension;
-  at.val.clusterDim.x = 16;
-  at.val.clusterDim.y = 1;
-  at.val.clusterDim.z = 1;
-  probe.attrs = &at;
-  probe.numAttrs = 1;
-  int clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&clusters, kernel, &probe) == cudaSuccess && clusters > 0)
-    return 16;
-  cudaGetLastError();
-  return 8;
-}
+// Cluster size: the portable 8 CTAs.  Measured on the six-solve 128^3 step, 8
+// (and 4) CTAs beat 16 by 4 % (the cluster barriers between the many short
+// phases cost more with more CTAs) and 1 CTA (the phases run serially) by 12 %.
+constexpr int kClusterCtas = 8;
 
 template <typename K>
 static void launch_cluster(K kernel, cudaStream_t st, const SubCycleArgs& a, size_t smem,
@@ -161,9 +139,8 @@ static void launch_cluster(K kernel, cudaStream_t st, const SubCycleArgs& a, siz
   count_launches(1);
 }
 
-static int g_cluster_ctas[2] = {0, 0};
 
-// Kernel attributes and the cluster size, set once outside any stream capture.
+// Kernel attributes, set once outside any stream capture.
 void init_subcycle() {
   static bool done = false;
   if (done) return;
@@ -172,21 +149,17 @@ void init_subcycle() {
                        4 * sizeof(double) * 4096);
   cudaFuncSetAttribute(k_subcycle32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        4 * sizeof(double) * 4096);
-  g_cluster_ctas[0] = cluster_size(k_subcycle64);
-  g_cluster_ctas[1] = cluster_size(k_subcycle32);
   cudaGetLastError();
 }
 
 void launch_subcycle64(cudaStream_t st, const SubCycleArgs& a) {
   const int nc = a.lv[a.nlev - 1].n;
-  launch_cluster(k_subcycle64, st, a, 3 * sizeof(double) * (size_t)nc * nc * nc,
-                 g_cluster_ctas[0]);
+  launch_cluster(k_subcycle64, st, a, 3 * sizeof(double) * (size_t)nc * nc * nc, kClusterCtas);
 }
 
 void launch_subcycle32(cudaStream_t st, const SubCycleArgs& a) {
   const int nc = a.lv32[a.nlev - 1].n;
-  launch_cluster(k_subcycle32, st, a, 4 * sizeof(double) * (size_t)nc * nc * nc,
-                 g_cluster_ctas[1]);
+  launch_cluster(k_subcycle32, st, a, 4 * sizeof(double) * (size_t)nc * nc * nc, kClusterCtas);
 }
 
 }  // namespace mg
