@@ -171,7 +171,11 @@ mg_status mg_assign_density(mg_grid* g, int level, int scheme, long long count, 
     dpos = tmp;
     dmass = mass ? tmp + 3 * count : nullptr;
   }
-  MG_CK(cudaMemsetAsync(G.rho, 0, sizeof(double) * cells, g->stream));
+  const cudaError_t ez = cudaMemsetAsync(G.rho, 0, sizeof(double) * cells, g->stream);
+  if (ez != cudaSuccess) {
+    if (tmp) cudaFree(tmp);
+    MG_FAIL(MG_ECUDA, cudaGetErrorString(ez));
+  }
   const unsigned nb = blocks_of(count, 256);
   if (scheme == MG_TSC)
     k_assign<2><<<nb, 256, 0, g->stream>>>(count, dpos, dpos + count, dpos + 2 * count, dmass,
