@@ -5,7 +5,8 @@
 
 Runs a single periodic solve (sigma 1.5, seed 1302) to 1e-8 on cuda:0, or with
 --six the six solves of one step of the benchmark, and prints the statistics of
-each solve as one JSON line.  Meant to be run under a profiler with a kernel
+each solve as one JSON line.  --case selects the other kernel families: a
+refined hierarchy, the batched solves, or particle assignment with refinement.  Meant to be run under a profiler with a kernel
 filter (for instance `ncu -k regex:k_smooth_colour64 -s 4 -c 3 ...`): at n = 256
 every FP64 array of the finest level is 134 MB, larger than the 126 MB L2, so
 DRAM counters describe HBM traffic.
@@ -33,12 +34,18 @@ def main(argv=None):
                    help="run the six solves of one benchmark step (128^3 lognormal, "
                         "r_V = 2, 8, 32 cells, both signs) instead of a single solve")
     p.add_argument("--sweep32", type=int, default=0)
+    p.add_argument("--case", choices=["solve", "refined", "batch", "particles"], default="solve",
+                   help="refined: a 128^3 sigma 2.0 domain with two refinement levels "
+                        "(alpha*kappa 1e-3); batch: the 64-solve mixed batch; particles: "
+                        "TSC assignment of 2^24 particles and the N_pc = 9 criterion at 256^3")
     args = p.parse_args(argv)
 
     import torch
 
     from paper_1303_0008_gb300 import inputs, mg
 
+    if args.case != "solve":
+        return other_case(args, torch, inputs, mg)
     prec = mg.MG_FP64 if args.prec == "fp64" else mg.MG_MIXED
     if args.six:
         w = inputs.workload_lognormal_sweep(128, 1.5, 1302)
@@ -64,6 +71,51 @@ def main(argv=None):
         mg.mg_destroy_grid(g)
     for st in out:
         print(json.dumps({"n": n, "prec": args.prec, **st}))
+
+
+def other_case(args, torch, inputs, mg):
+    import numpy as np
+    if args.case == "refined":
+        h = inputs.refined_hierarchy(128, 2.0, 1303)
+        g = mg.mg_create_grid(128)
+        try:
+            mg.mg_set_density(g, 0, -1, h["delta0"])
+            for lvl, L in enumerate(h["levels"], start=1):
+                mg.mg_add_patches(g, lvl, L["origins"])
+                mg.mg_set_density(g, lvl, -1, np.ascontiguousarray(L["delta"]))
+            st = mg.mg_solve(g, 0, 1e-3, 1.0, args.tol)
+            levels = [mg.mg_get_level_stats(g, lvl)["cycles"] for lvl in (1, 2)]
+        finally:
+            mg.mg_destroy_grid(g)
+        print(json.dumps({"case": "refined", "domain_cycles": st["cycles"], "level_cycles": levels,
+                          "patches": [len(L["origins"]) for L in h["levels"]]}))
+    elif args.case == "batch":
+        w = inputs.workload_batch(64)
+        g = mg.mg_create_batch([s["n"] for s in w], mg.options(prec=mg.MG_MIXED))
+        try:
+            for k, s in enumerate(w):
+                mg.mg_set_density(g, 0, k, inputs.lognormal_delta(s["n"], s["sigma"], s["seed"]))
+            rc, stats = mg.mg_solve_batch(g, [s["branch"] for s in w], [s["alpha"] for s in w],
+                                          [s["kappa"] for s in w], args.tol)
+        finally:
+            mg.mg_destroy_grid(g)
+        print(json.dumps({"case": "batch", "rc": rc, "max_outer": max(s["outer"] for s in stats)}))
+    else:
+        n, count = 256, 1 << 24
+        gen = torch.Generator(device="cuda").manual_seed(1307)
+        pos = torch.rand((3, count), generator=gen, dtype=torch.float64, device="cuda")
+        pos[:, : count // 2] = torch.remainder(
+            0.5 + 0.03 * torch.randn((3, count // 2), generator=gen, dtype=torch.float64,
+                                     device="cuda"), 1.0)
+        g = mg.mg_create_grid(n)
+        try:
+            mg.mg_assign_density(g, 0, pos.contiguous())
+            org = mg.mg_refine_blocks(g, 0, 9.0, 1.0 / count)
+            mg.mg_add_patches(g, 1, org)
+            mg.mg_assign_density(g, 1, pos.contiguous())
+        finally:
+            mg.mg_destroy_grid(g)
+        print(json.dumps({"case": "particles", "patches": int(len(org))}))
 
 
 if __name__ == "__main__":
