@@ -308,7 +308,10 @@ __device__ __forceinline__ void b_residual_restrict32(
   if (t < ccells) {
     int I, J, K;
     split3((unsigned)t, nc, I, J, K);
-    float se_sum = 0.f, sr = 0.f;
+    // norms of the 8 children in FP32 (the inner problem's lambda needs FP32
+    // accuracy only), merged into the FP64 block partial once per thread
+    float se_sum = 0.f, sr = 0.f, fsum = 0.f, fmx = -INFINITY, fmn = INFINITY;
+    int bad = 0;
 #pragma unroll 1
     for (int ch = 0; ch < 8; ++ch) {
       const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
@@ -322,10 +325,22 @@ __device__ __forceinline__ void b_residual_restrict32(
       const float ctr = e[id];
       const float lap = (se.sx + se.sy + se.sz) - 6.f * ctr;
       const float r = fmaf(lap, c.inv_h2, -dd) - g[id];
-      partial_add(p, (double)r, false);
+      if (isfinite(r)) {
+        fsum += r;
+        fmx = fmaxf(fmx, r);
+        fmn = fminf(fmn, r);
+      } else {
+        ++bad;
+      }
       se_sum += ctr;
       sr += r;
     }
+    if (bad < 8) {
+      p.sum = (double)fsum;
+      p.dmax = (double)fmx;
+      p.dmin = (double)fmn;
+    }
+    p.nonfinite = bad;
     e_c[t] = se_sum * 0.125f;
     ehat_c[t] = se_sum * 0.125f;
     rg_c[t] = sr * 0.125f;
