@@ -193,18 +193,14 @@ __device__ __forceinline__ void b_q0_prep32(int n, const float* __restrict__ phi
   q0[t] = fmaf(c.c3, c.g1 * A + c.g2 * B, qs);
 }
 
-__device__ __forceinline__ void b_smooth_colour32(int n, float* __restrict__ e,
-                                                         const float* __restrict__ phi0,
-                                                         const float* __restrict__ q0,
-                                                         const float* __restrict__ g,
-                                                         const LevelScalars* __restrict__ sc,
-                                                         OpConst32 c, int colour,
-    long long blk) {
-  __shared__ float s_mu;
-  if (threadIdx.x == 0) s_mu = (float)sc->lambda;
-  __syncthreads();
+// One cell of an FP32 colour stage: t indexes the colour's n^3/4 cells; t >= n^3/4
+// does nothing.  mu is the level's lambda in FP32.
+__device__ __forceinline__ void cell_smooth32(int n, float* __restrict__ e,
+                                              const float* __restrict__ phi0,
+                                              const float* __restrict__ q0,
+                                              const float* __restrict__ g, float mu,
+                                              const OpConst32& c, int colour, long long t) {
   const int hn = n >> 1;
-  const long long t = (long long)blk * blockDim.x + threadIdx.x;
   const long long total = (long long)hn * hn * n;
   if (t >= total) return;
   int m, jj, k;
@@ -216,7 +212,20 @@ __device__ __forceinline__ void b_smooth_colour32(int n, float* __restrict__ e,
   const StencilT<float> se = gather_at(e + id, o);
   float dd = 0.f;
   if (!c.linear) dd = dD32(se, gather_at(phi0 + id, o), q0[id], c);
-  e[id] = gs_value32(se, dd, g[id], s_mu, c);
+  e[id] = gs_value32(se, dd, g[id], mu, c);
+}
+
+__device__ __forceinline__ void b_smooth_colour32(int n, float* __restrict__ e,
+                                                         const float* __restrict__ phi0,
+                                                         const float* __restrict__ q0,
+                                                         const float* __restrict__ g,
+                                                         const LevelScalars* __restrict__ sc,
+                                                         OpConst32 c, int colour,
+    long long blk) {
+  __shared__ float s_mu;
+  if (threadIdx.x == 0) s_mu = (float)sc->lambda;
+  __syncthreads();
+  cell_smooth32(n, e, phi0, q0, g, s_mu, c, colour, (long long)blk * blockDim.x + threadIdx.x);
 }
 
 // The colour stage of b_smooth_colour32 with two cells per thread: the cells
@@ -294,6 +303,24 @@ __device__ __forceinline__ void b_smooth_colour32_pair(int n, float* __restrict_
   ea[2] = v.y;
 }
 
+// The FP32 defect r = N(e) - g of fine cell (i,j,k) (linear index id); ctr
+// returns e there.
+__device__ __forceinline__ float fine_defect32(int nf, const float* __restrict__ e,
+                                              const float* __restrict__ phi0,
+                                              const float* __restrict__ q0,
+                                              const float* __restrict__ g, const OpConst32& c,
+                                              int i, int j, int k, long long id, float& ctr) {
+  const StencilT<float> se = gather_periodic(e, i, j, k, nf);
+  float dd = 0.f;
+  if (!c.linear) {
+    const StencilT<float> sp = gather_periodic(phi0, i, j, k, nf);
+    dd = dD32(se, sp, q0[id], c);
+  }
+  ctr = e[id];
+  const float lap = (se.sx + se.sy + se.sz) - 6.f * ctr;
+  return fmaf(lap, c.inv_h2, -dd) - g[id];
+}
+
 __device__ __forceinline__ void b_residual_restrict32(
     int nf, const float* __restrict__ e, const float* __restrict__ phi0,
     const float* __restrict__ q0, const float* __restrict__ g, OpConst32 c,
@@ -316,15 +343,8 @@ __device__ __forceinline__ void b_residual_restrict32(
     for (int ch = 0; ch < 8; ++ch) {
       const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
       const long long id = lidx(i, j, k, nf);
-      const StencilT<float> se = gather_periodic(e, i, j, k, nf);
-      float dd = 0.f;
-      if (!c.linear) {
-        const StencilT<float> sp = gather_periodic(phi0, i, j, k, nf);
-        dd = dD32(se, sp, q0[id], c);
-      }
-      const float ctr = e[id];
-      const float lap = (se.sx + se.sy + se.sz) - 6.f * ctr;
-      const float r = fmaf(lap, c.inv_h2, -dd) - g[id];
+      float ctr;
+      const float r = fine_defect32(nf, e, phi0, q0, g, c, i, j, k, id, ctr);
       if (isfinite(r)) {
         fsum += r;
         fmx = fmaxf(fmx, r);
@@ -349,15 +369,74 @@ __device__ __forceinline__ void b_residual_restrict32(
   if (threadIdx.x == 0) partials[blk] = p;
 }
 
-__device__ __forceinline__ void b_fas_rhs32(int nc, const float* __restrict__ e_c,
-                                                   const float* __restrict__ phi0_c,
-                                                   const float* __restrict__ q0_c,
-                                                   float* __restrict__ g_c, OpConst32 c,
-                                                   const LevelScalars* __restrict__ fine_sc,
-                                                   LevelScalars* __restrict__ coarse_sc,
+// The FP32 residual restriction in two steps (as cell_defect64 and
+// b_restrict_defects64): per fine cell r, then every coarse cell's 8 children in
+// the order and block partition of b_residual_restrict32.
+__device__ __forceinline__ void cell_defect32(int nf, const float* __restrict__ e,
+                                              const float* __restrict__ phi0,
+                                              const float* __restrict__ q0,
+                                              const float* __restrict__ g, const OpConst32& c,
+                                              float* __restrict__ rout, long long t) {
+  const long long cells = (long long)nf * nf * nf;
+  if (t >= cells) return;
+  int i, j, k;
+  split3((unsigned)t, nf, i, j, k);
+  float ctr;
+  rout[t] = fine_defect32(nf, e, phi0, q0, g, c, i, j, k, t, ctr);
+}
+
+__device__ __forceinline__ void b_restrict_defects32(
+    int nf, const float* __restrict__ e, const float* __restrict__ rin, float* __restrict__ e_c,
+    float* __restrict__ ehat_c, float* __restrict__ rg_c, Partial* __restrict__ partials,
     long long blk) {
-  const long long cells = (long long)nc * nc * nc;
+  const int nc = nf >> 1;
+  const long long ccells = (long long)nc * nc * nc;
   const long long t = (long long)blk * blockDim.x + threadIdx.x;
+  Partial p;
+  partial_init(p);
+  if (t < ccells) {
+    int I, J, K;
+    split3((unsigned)t, nc, I, J, K);
+    float se_sum = 0.f, sr = 0.f, fsum = 0.f, fmx = -INFINITY, fmn = INFINITY;
+    int bad = 0;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+      const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
+      const long long id = lidx(i, j, k, nf);
+      const float r = rin[id];
+      if (isfinite(r)) {
+        fsum += r;
+        fmx = fmaxf(fmx, r);
+        fmn = fminf(fmn, r);
+      } else {
+        ++bad;
+      }
+      se_sum += e[id];
+      sr += r;
+    }
+    if (bad < 8) {
+      p.sum = (double)fsum;
+      p.dmax = (double)fmx;
+      p.dmin = (double)fmn;
+    }
+    p.nonfinite = bad;
+    e_c[t] = se_sum * 0.125f;
+    ehat_c[t] = se_sum * 0.125f;
+    rg_c[t] = sr * 0.125f;
+  }
+  p = block_reduce(p);
+  if (threadIdx.x == 0) partials[blk] = p;
+}
+
+// One coarse cell of the FP32 FAS right-hand side (t indexes the nc^3 cells; lam_f
+// is the fine level's lambda; cell 0 also clears the coarse lambda).
+__device__ __forceinline__ void cell_fas_rhs32(int nc, const float* __restrict__ e_c,
+                                               const float* __restrict__ phi0_c,
+                                               const float* __restrict__ q0_c,
+                                               float* __restrict__ g_c, const OpConst32& c,
+                                               double lam_f, LevelScalars* __restrict__ coarse_sc,
+                                               long long t) {
+  const long long cells = (long long)nc * nc * nc;
   if (t == 0) coarse_sc->lambda = 0.0;
   if (t >= cells) return;
   int i, j, k;
@@ -370,16 +449,27 @@ __device__ __forceinline__ void b_fas_rhs32(int nc, const float* __restrict__ e_
   }
   const float lap = (se.sx + se.sy + se.sz) - 6.f * e_c[t];
   const float Nv = fmaf(lap, c.inv_h2, -dd);
-  g_c[t] = Nv - g_c[t] + (float)fine_sc->lambda;
+  g_c[t] = Nv - g_c[t] + (float)lam_f;
 }
 
-__device__ __forceinline__ void b_prolong_correct32(int nc, const float* __restrict__ e_c,
-                                                           const float* __restrict__ ehat_c,
-                                                           float* __restrict__ e_f,
+__device__ __forceinline__ void b_fas_rhs32(int nc, const float* __restrict__ e_c,
+                                                   const float* __restrict__ phi0_c,
+                                                   const float* __restrict__ q0_c,
+                                                   float* __restrict__ g_c, OpConst32 c,
+                                                   const LevelScalars* __restrict__ fine_sc,
+                                                   LevelScalars* __restrict__ coarse_sc,
     long long blk) {
+  cell_fas_rhs32(nc, e_c, phi0_c, q0_c, g_c, c, fine_sc->lambda, coarse_sc,
+                 (long long)blk * blockDim.x + threadIdx.x);
+}
+
+// One fine cell of the trilinear prolongation of e_c - ehat_c into e_f (t indexes
+// the (2 nc)^3 fine cells).
+__device__ __forceinline__ void cell_prolong32(int nc, const float* __restrict__ e_c,
+                                               const float* __restrict__ ehat_c,
+                                               float* __restrict__ e_f, long long t) {
   const int nf = nc << 1;
   const long long cells = (long long)nf * nf * nf;
-  const long long t = (long long)blk * blockDim.x + threadIdx.x;
   if (t >= cells) return;
   int i, j, k;
   split3((unsigned)t, nf, i, j, k);
@@ -394,6 +484,13 @@ __device__ __forceinline__ void b_prolong_correct32(int nc, const float* __restr
   const float s = 27.f * v(I0, J0, K0) + 9.f * (v(I1, J0, K0) + v(I0, J1, K0) + v(I0, J0, K1)) +
                   3.f * (v(I1, J1, K0) + v(I1, J0, K1) + v(I0, J1, K1)) + v(I1, J1, K1);
   e_f[t] += s * (1.f / 64.f);
+}
+
+__device__ __forceinline__ void b_prolong_correct32(int nc, const float* __restrict__ e_c,
+                                                           const float* __restrict__ ehat_c,
+                                                           float* __restrict__ e_f,
+    long long blk) {
+  cell_prolong32(nc, e_c, ehat_c, e_f, (long long)blk * blockDim.x + threadIdx.x);
 }
 
 __device__ __forceinline__ void b_coarsest_corr64(int n, float* __restrict__ e,

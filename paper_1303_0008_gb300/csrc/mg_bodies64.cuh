@@ -1,30 +1,33 @@
-// Per-thread bodies of the FP64 kernels of mg_fp64.cu.  Each body takes the
+// Per-thread bodies of the FP64 kernels of mg_fp64.cu.  Each b_* body takes the
 // block index as an argument so that the single-grid kernels (blk = blockIdx.x)
 // and the batched work-list kernels of mg_batch.cu (blk = block within its item)
-// run the same code.
+// run the same code; the cell_* functions take the item index itself, so that
+// the cluster sub-cycle (mg_subcycle.cu) can spread items over its CTAs freely.
 #pragma once
 
 #include "mg_common.cuh"
 
 namespace mg {
 
-__device__ __forceinline__ void b_smooth_colour64(int n, double* __restrict__ phi,
-                                                         const double* __restrict__ src,
-                                                         const double* __restrict__ f,
-                                                         const LevelScalars* __restrict__ sc,
-                                                         OpConst64 c, int colour,
-    long long blk) {
+// The block-wide constant of a colour stage (thread 0 computes it into shared
+// memory): -h^2 (lambda - k2)/6 in the sqrt form, -h^2 lambda/6 in the root form,
+// lambda itself for OP_GENW.
+__device__ __forceinline__ double smooth_scalar64(const LevelScalars* __restrict__ sc,
+                                                  const OpConst64& c) {
+  return c.mode == OP_GENW ? sc->lambda
+                           : -c.h2_6 * (c.mode == OP_SQRT ? sc->lambda - c.k2 : sc->lambda);
+}
+
+// One cell of a colour stage: t indexes the colour's n^3/4 cells; t >= n^3/4 does
+// nothing.
+__device__ __forceinline__ void cell_smooth64(int n, double* __restrict__ phi,
+                                              const double* __restrict__ src,
+                                              const double* __restrict__ f, double s_c,
+                                              const OpConst64& c, int colour, long long t) {
   // phi_new = (Sx + Sy + Sz - h^2 (D + f + lambda)) / 6.  In the sqrt form,
   // D = k2s sqrt(q) - k2, so phi_new = upd_s sqrt(q) + (Sx+Sy+Sz)/6 - h^2 f/6 + C with
-  // the block-wide C = -h^2 (lambda - k2)/6.
-  __shared__ double s_c;
-  // (OP_GENW keeps lambda itself here: its update is the Newton step below)
-  if (threadIdx.x == 0)
-    s_c = c.mode == OP_GENW ? sc->lambda
-                            : -c.h2_6 * (c.mode == OP_SQRT ? sc->lambda - c.k2 : sc->lambda);
-  __syncthreads();
+  // the block-wide C = -h^2 (lambda - k2)/6 (s_c).
   const int hn = n >> 1;
-  const long long t = (long long)blk * blockDim.x + threadIdx.x;
   const long long total = (long long)hn * hn * n;
   if (t >= total) return;
   int m, jj, k;
@@ -58,6 +61,34 @@ __device__ __forceinline__ void b_smooth_colour64(int n, double* __restrict__ ph
   phi[id] = v;
 }
 
+__device__ __forceinline__ void b_smooth_colour64(int n, double* __restrict__ phi,
+                                                         const double* __restrict__ src,
+                                                         const double* __restrict__ f,
+                                                         const LevelScalars* __restrict__ sc,
+                                                         OpConst64 c, int colour,
+    long long blk) {
+  __shared__ double s_c;
+  if (threadIdx.x == 0) s_c = smooth_scalar64(sc, c);
+  __syncthreads();
+  cell_smooth64(n, phi, src, f, s_c, c, colour, (long long)blk * blockDim.x + threadIdx.x);
+}
+
+// The defect d = L(phi) - f of fine cell (i,j,k) (linear index id) and its guard
+// flag; ctr returns phi there.
+__device__ __forceinline__ double fine_defect64(int nf, const double* __restrict__ phi,
+                                               const double* __restrict__ src,
+                                               const double* __restrict__ f,
+                                               const OpConst64& c, int i, int j, int k,
+                                               long long id, double& ctr, bool& g) {
+  const StencilT<double> s = gather_periodic(phi, i, j, k, nf);
+  ctr = phi[id];
+  const double D = root_Dc(s, ctr, src[id], c, g);
+  const double lap = (s.sx + s.sy + s.sz) - 6.0 * ctr;
+  double d = fma(lap, c.inv_h2, -D);
+  if (f) d -= f[id];
+  return d;
+}
+
 __device__ __forceinline__ void b_residual_restrict64(
     int nf, const double* __restrict__ phi, const double* __restrict__ src,
     const double* __restrict__ f, OpConst64 c, double* __restrict__ phi_c,
@@ -76,13 +107,9 @@ __device__ __forceinline__ void b_residual_restrict64(
     for (int ch = 0; ch < 8; ++ch) {
       const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
       const long long id = lidx(i, j, k, nf);
-      const StencilT<double> s = gather_periodic(phi, i, j, k, nf);
       bool g;
-      const double ctr = phi[id];
-      const double D = root_Dc(s, ctr, src[id], c, g);
-      const double lap = (s.sx + s.sy + s.sz) - 6.0 * ctr;
-      double d = fma(lap, c.inv_h2, -D);
-      if (f) d -= f[id];
+      double ctr;
+      const double d = fine_defect64(nf, phi, src, f, c, i, j, k, id, ctr, g);
       partial_add(p, d, g);
       sphi += ctr;
       sd += d;
@@ -95,34 +122,99 @@ __device__ __forceinline__ void b_residual_restrict64(
   if (threadIdx.x == 0) partials[blk] = p;
 }
 
+// The residual restriction in two steps, for launches whose per-coarse-cell
+// loop would leave most SMs idle: cell_defect64 stores each fine cell's defect
+// and guard flag (t indexes the nf^3 fine cells), then b_restrict_defects64
+// walks every coarse cell's 8 children in the order of b_residual_restrict64,
+// with its block partition, so both give the same bits.
+__device__ __forceinline__ void cell_defect64(int nf, const double* __restrict__ phi,
+                                              const double* __restrict__ src,
+                                              const double* __restrict__ f, const OpConst64& c,
+                                              double* __restrict__ dout,
+                                              unsigned char* __restrict__ gout, long long t) {
+  const long long cells = (long long)nf * nf * nf;
+  if (t >= cells) return;
+  int i, j, k;
+  split3((unsigned)t, nf, i, j, k);
+  bool g;
+  double ctr;
+  dout[t] = fine_defect64(nf, phi, src, f, c, i, j, k, t, ctr, g);
+  gout[t] = g ? 1 : 0;
+}
+
+__device__ __forceinline__ void b_restrict_defects64(
+    int nf, const double* __restrict__ phi, const double* __restrict__ din,
+    const unsigned char* __restrict__ gin, double* __restrict__ phi_c,
+    double* __restrict__ phihat_c, double* __restrict__ rd_c, Partial* __restrict__ partials,
+    long long blk) {
+  const int nc = nf >> 1;
+  const long long ccells = (long long)nc * nc * nc;
+  const long long t = (long long)blk * blockDim.x + threadIdx.x;
+  Partial p;
+  partial_init(p);
+  if (t < ccells) {
+    int I, J, K;
+    split3((unsigned)t, nc, I, J, K);
+    double sphi = 0.0, sd = 0.0;
+#pragma unroll
+    for (int ch = 0; ch < 8; ++ch) {
+      const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
+      const long long id = lidx(i, j, k, nf);
+      const double d = din[id];
+      partial_add(p, d, gin[id] != 0);
+      sphi += phi[id];
+      sd += d;
+    }
+    phi_c[t] = sphi * 0.125;
+    phihat_c[t] = sphi * 0.125;
+    rd_c[t] = sd * 0.125;
+  }
+  p = block_reduce(p);
+  if (threadIdx.x == 0) partials[blk] = p;
+}
+
+// The level norms from the per-block partials: the block-wide merge of b_finalize
+// (thread 0 holds the result), and the scalars it stores.
+__device__ __forceinline__ Partial merge_partials(const Partial* __restrict__ partials,
+                                                  int nparts) {
+  Partial p;
+  partial_init(p);
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) partial_merge(p, partials[b]);
+  return block_reduce(p);
+}
+
+__device__ __forceinline__ double level_lambda(const Partial& p, double cells, int periodic) {
+  return periodic ? p.sum / cells : 0.0;
+}
+
+__device__ __forceinline__ void store_scalars(const Partial& p, double lam,
+                                              LevelScalars* __restrict__ sc) {
+  sc->lambda = lam;
+  sc->sum = p.sum;
+  sc->dmax = p.dmax;
+  sc->dmin = p.dmin;
+  sc->res = (p.nonfinite > 0) ? NAN : fmax(p.dmax - lam, lam - p.dmin);
+  sc->guards = p.guards;
+  sc->nonfinite = p.nonfinite;
+}
+
 __device__ __forceinline__ void b_finalize(const Partial* __restrict__ partials, int nparts,
                                                   double cells, int periodic,
                                                   LevelScalars* __restrict__ sc,
     long long blk) {
-  Partial p;
-  partial_init(p);
-  for (int b = threadIdx.x; b < nparts; b += blockDim.x) partial_merge(p, partials[b]);
-  p = block_reduce(p);
-  if (threadIdx.x == 0) {
-    const double lam = periodic ? p.sum / cells : 0.0;
-    sc->lambda = lam;
-    sc->sum = p.sum;
-    sc->dmax = p.dmax;
-    sc->dmin = p.dmin;
-    sc->res = (p.nonfinite > 0) ? NAN : fmax(p.dmax - lam, lam - p.dmin);
-    sc->guards = p.guards;
-    sc->nonfinite = p.nonfinite;
-  }
+  const Partial p = merge_partials(partials, nparts);
+  if (threadIdx.x == 0) store_scalars(p, level_lambda(p, cells, periodic), sc);
 }
 
-__device__ __forceinline__ void b_fas_rhs64(int nc, const double* __restrict__ phi_c,
-                                                   const double* __restrict__ src_c,
-                                                   double* __restrict__ f_c, OpConst64 c,
-                                                   const LevelScalars* __restrict__ fine_sc,
-                                                   LevelScalars* __restrict__ coarse_sc,
-    long long blk) {
+// One coarse cell of the FAS right-hand side f_c = L_c(phi_c) - f_c + lambda_f
+// (t indexes the nc^3 cells; lam_f is the fine level's lambda; cell 0 also clears
+// the coarse lambda).
+__device__ __forceinline__ void cell_fas_rhs64(int nc, const double* __restrict__ phi_c,
+                                               const double* __restrict__ src_c,
+                                               double* __restrict__ f_c, const OpConst64& c,
+                                               double lam_f, LevelScalars* __restrict__ coarse_sc,
+                                               long long t) {
   const long long cells = (long long)nc * nc * nc;
-  const long long t = (long long)blk * blockDim.x + threadIdx.x;
   if (t == 0) coarse_sc->lambda = 0.0;
   if (t >= cells) return;
   int i, j, k;
@@ -132,16 +224,26 @@ __device__ __forceinline__ void b_fas_rhs64(int nc, const double* __restrict__ p
   const double D = root_Dc(s, phi_c[t], src_c[t], c, g);
   const double lap = (s.sx + s.sy + s.sz) - 6.0 * phi_c[t];
   const double L = fma(lap, c.inv_h2, -D);
-  f_c[t] = L - f_c[t] + fine_sc->lambda;
+  f_c[t] = L - f_c[t] + lam_f;
 }
 
-__device__ __forceinline__ void b_prolong_correct64(int nc, const double* __restrict__ phi_c,
-                                                           const double* __restrict__ phihat_c,
-                                                           double* __restrict__ phi_f,
+__device__ __forceinline__ void b_fas_rhs64(int nc, const double* __restrict__ phi_c,
+                                                   const double* __restrict__ src_c,
+                                                   double* __restrict__ f_c, OpConst64 c,
+                                                   const LevelScalars* __restrict__ fine_sc,
+                                                   LevelScalars* __restrict__ coarse_sc,
     long long blk) {
+  cell_fas_rhs64(nc, phi_c, src_c, f_c, c, fine_sc->lambda, coarse_sc,
+                 (long long)blk * blockDim.x + threadIdx.x);
+}
+
+// One fine cell of the trilinear prolongation of the coarse correction
+// phi_c - phihat_c, added to phi_f (t indexes the (2 nc)^3 fine cells).
+__device__ __forceinline__ void cell_prolong64(int nc, const double* __restrict__ phi_c,
+                                               const double* __restrict__ phihat_c,
+                                               double* __restrict__ phi_f, long long t) {
   const int nf = nc << 1;
   const long long cells = (long long)nf * nf * nf;
-  const long long t = (long long)blk * blockDim.x + threadIdx.x;
   if (t >= cells) return;
   int i, j, k;
   split3((unsigned)t, nf, i, j, k);
@@ -156,6 +258,13 @@ __device__ __forceinline__ void b_prolong_correct64(int nc, const double* __rest
   const double v = 27.0 * e(I0, J0, K0) + 9.0 * (e(I1, J0, K0) + e(I0, J1, K0) + e(I0, J0, K1)) +
                    3.0 * (e(I1, J1, K0) + e(I1, J0, K1) + e(I0, J1, K1)) + e(I1, J1, K1);
   phi_f[t] += v * (1.0 / 64.0);
+}
+
+__device__ __forceinline__ void b_prolong_correct64(int nc, const double* __restrict__ phi_c,
+                                                           const double* __restrict__ phihat_c,
+                                                           double* __restrict__ phi_f,
+    long long blk) {
+  cell_prolong64(nc, phi_c, phihat_c, phi_f, (long long)blk * blockDim.x + threadIdx.x);
 }
 
 __device__ __forceinline__ void b_coarsest64(int n, double* __restrict__ phi,

@@ -82,6 +82,11 @@ mg_status domain_create(Domain** out, int n, const mg_options& o) {
   }
   d->part_cap = partials_needed(d->lv[0].cells);
   ok = ok && cudaMalloc(&d->d_part, sizeof(Partial) * d->part_cap) == cudaSuccess;
+  {
+    const size_t sub = (size_t)kSubcycleMaxN * kSubcycleMaxN * kSubcycleMaxN;
+    ok = ok && cudaMalloc(&d->d_subdef, sizeof(double) * sub) == cudaSuccess;
+    ok = ok && cudaMalloc(&d->d_subguard, sub) == cudaSuccess;
+  }
   ok = ok && cudaMalloc(&d->d_sc, sizeof(LevelScalars) * (2 * nl + 2)) == cudaSuccess;
   ok = ok && cudaMallocHost(&d->h_sc, sizeof(LevelScalars) * 2) == cudaSuccess;
   if (!ok) {
@@ -120,6 +125,8 @@ void domain_destroy(Domain* d) {
   }
   mixed_release(d);
   cudaFree(d->d_part);
+  cudaFree(d->d_subdef);
+  cudaFree(d->d_subguard);
   cudaFree(d->d_sc);
   if (d->h_sc) cudaFreeHost(d->h_sc);
   delete d;
@@ -151,6 +158,8 @@ struct Cycle64 {
       a.lv[k] = SubLevel64{L.n, L.phi, L.src, L.f, L.phihat, d->d_sc + l + k, ops[l + k]};
     }
     a.part = d->d_part;
+    a.def64 = d->d_subdef;
+    a.guard = d->d_subguard;
     a.nu_pre = o->nu_pre;
     a.nu_post = o->nu_post;
     a.coarse_sweeps = o->coarse_sweeps;

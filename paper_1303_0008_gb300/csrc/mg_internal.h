@@ -158,8 +158,9 @@ namespace mg {
 
 // Levels at or below this side run their whole sub-V-cycle in one launch of a
 // single thread-block cluster (see mg_subcycle.cu).
-// levels with more cells per side run faster as per-level launches (measured with
-// 32 for both precisions: the six-solve 128^3 step slowed by 13 % (FP64) and 9 % (mixed))
+// levels with more cells per side run faster as per-level launches (entering the
+// sub-cycle at 32 slowed the six-solve 128^3 step by 3.5 % (FP64) and left the
+// mixed step unchanged)
 constexpr int kSubcycleMaxN = 16;
 constexpr int kSubcycleMaxLevels = 8;
 
@@ -182,6 +183,9 @@ struct SubCycleArgs {
   SubLevel64 lv[kSubcycleMaxLevels];
   SubLevel32 lv32[kSubcycleMaxLevels];
   Partial* part;
+  double* def64;          // kSubcycleMaxN^3 fine-cell defects (FP64 cycle)
+  float* def32;           // the same for the FP32 cycle
+  unsigned char* guard;   // kSubcycleMaxN^3 guard flags (FP64 cycle)
   int nu_pre, nu_post, coarse_sweeps;
   double coarse_drop;
 };

@@ -259,6 +259,7 @@ struct CycleMixed {
       a.lv32[k] = SubLevel32{L.n, L.e, L.ehat, L.phi0, L.q0, L.rhs, sc32(l + k), ops32[l + k]};
     }
     a.part = d->d_part;
+    a.def32 = reinterpret_cast<float*>(d->d_subdef);
     a.nu_pre = o->nu_pre;
     a.nu_post = o->nu_post;
     a.coarse_sweeps = o->coarse_sweeps;
