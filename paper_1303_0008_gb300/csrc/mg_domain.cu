@@ -83,7 +83,9 @@ mg_status domain_create(Domain** out, int n, const mg_options& o) {
   d->part_cap = partials_needed(d->lv[0].cells);
   ok = ok && cudaMalloc(&d->d_part, sizeof(Partial) * d->part_cap) == cudaSuccess;
   {
-    const size_t sub = (size_t)kSubcycleMaxN * kSubcycleMaxN * kSubcycleMaxN;
+    static_assert(kTwoStepMaxFine >= (long long)kSubcycleMaxN * kSubcycleMaxN * kSubcycleMaxN,
+                  "the two-step scratch also serves the sub-cycle");
+    const size_t sub = (size_t)kTwoStepMaxFine;
     ok = ok && cudaMalloc(&d->d_subdef, sizeof(double) * sub) == cudaSuccess;
     ok = ok && cudaMalloc(&d->d_subguard, sub) == cudaSuccess;
   }
@@ -181,7 +183,7 @@ struct Cycle64 {
     Level& C = d->lv[l + 1];
     launch_smooth64(st, L.n, L.phi, L.src, L.f, sc, ops[l], o->nu_pre);
     launch_residual_restrict64(st, L.n, L.phi, L.src, L.f, ops[l], C.phi, C.phihat, C.f,
-                               d->d_part, sc);
+                               d->d_part, sc, d->d_subdef, d->d_subguard);
     launch_fas_rhs64(st, C.n, C.phi, C.src, C.f, ops[l + 1], sc, d->d_sc + l + 1);
     descend(l + 1);
     launch_prolong_correct64(st, C.n, C.phi, C.phihat, L.phi);
@@ -194,7 +196,7 @@ struct Cycle64 {
     Level& C = d->lv[1];
     launch_smooth64(st, L.n, L.phi, L.src, nullptr, d->d_sc, ops[0], o->nu_pre, timer_a);
     launch_residual_restrict64(st, L.n, L.phi, L.src, nullptr, ops[0], C.phi, C.phihat, C.f,
-                               d->d_part, d->d_sc);
+                               d->d_part, d->d_sc, d->d_subdef, d->d_subguard);
     cudaMemcpyAsync(d->h_sc, d->d_sc, sizeof(LevelScalars), cudaMemcpyDeviceToHost, st);
     if (o->tau_stop > 0.0) {
       // The first coarse FAS right-hand side is L^H(R phi) - R L^h(phi) + lambda^h, the

@@ -67,6 +67,27 @@ __global__ void __launch_bounds__(256) k_residual_restrict64(
   b_residual_restrict64(nf, phi, src, f, c, phi_c, phihat_c, rd_c, partials, blockIdx.x);
 }
 
+// The same residual restriction in two launches, for levels whose coarse cells
+// fill only a few 256-thread blocks: per fine cell the defect and guard flag
+// (blocks of any size), then the walk over each coarse cell's children in the
+// order and 256-thread partition of k_residual_restrict64 (the same bits).
+__global__ void __launch_bounds__(256) k_defect64(int nf, const double* __restrict__ phi,
+                                                  const double* __restrict__ src,
+                                                  const double* __restrict__ f, OpConst64 c,
+                                                  double* __restrict__ dout,
+                                                  unsigned char* __restrict__ gout) {
+  PdlScope pdl_scope;
+  cell_defect64(nf, phi, src, f, c, dout, gout, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(256) k_restrict_defects64(
+    int nf, const double* __restrict__ phi, const double* __restrict__ din,
+    const unsigned char* __restrict__ gin, double* __restrict__ phi_c,
+    double* __restrict__ phihat_c, double* __restrict__ rd_c, Partial* __restrict__ partials) {
+  PdlScope pdl_scope;
+  b_restrict_defects64(nf, phi, din, gin, phi_c, phihat_c, rd_c, partials, blockIdx.x);
+}
+
 // One block: reduce the partials in a fixed order and publish the scalars.
 __global__ void __launch_bounds__(256) k_finalize(const Partial* __restrict__ partials, int nparts,
                                                   double cells, int periodic,
@@ -221,13 +242,29 @@ void src_coefficients(const OpConst64& c, double kappa, double* a, double* b) {
 
 thread_local long long tl_launches = 0;
 
+// Threads per block of a per-cell FP64 launch: 256, or 64 where 256-thread
+// blocks would not give every SM two blocks.  An SM retires only two FP64
+// lane-operations per clock, so on small levels the launch time is set by how
+// many SMs the cells reach.  Per-cell results do not depend on the partition.
+int tpb_for(long long items) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms = v > 0 ? v : 1;
+  }
+  return (long long)blocks_for(items, 256) < 2LL * sms ? 64 : 256;
+}
+
 void launch_smooth64(cudaStream_t st, int n, double* phi, const double* src, const double* f,
                      const LevelScalars* sc, const OpConst64& c, int sweeps, EventPairs* timer) {
   const long long per = (long long)(n / 2) * (n / 2) * n;
+  const int tpb = tpb_for(per);
   for (int s = 0; s < sweeps; ++s)
     for (int colour = 0; colour < 4; ++colour) {
       if (timer) timer->begin(st);
-      launch_k(k_smooth_colour64, blocks_for(per, 256), 256, 0, st, n, phi, src, f, sc, c, colour);
+      launch_k(k_smooth_colour64, blocks_for(per, tpb), tpb, 0, st, n, phi, src, f, sc, c, colour);
       if (timer) timer->end(st);
     }
   count_launches(4LL * sweeps);
@@ -248,11 +285,21 @@ void launch_residual64(cudaStream_t st, int n, const double* phi, const double* 
 void launch_residual_restrict64(cudaStream_t st, int nf, const double* phi, const double* src,
                                 const double* f, const OpConst64& c, double* phi_c,
                                 double* phihat_c, double* rd_c, Partial* partials,
-                                LevelScalars* sc) {
-  const long long ccells = (long long)(nf / 2) * (nf / 2) * (nf / 2);
+                                LevelScalars* sc, double* def, unsigned char* guard) {
+  const long long fcells = (long long)nf * nf * nf;
+  const long long ccells = fcells / 8;
   const unsigned nb = blocks_for(ccells, 256);
-  launch_k(k_residual_restrict64, nb, 256, 0, st, nf, phi, src, f, c, phi_c, phihat_c, rd_c, partials);
-  launch_k(k_finalize, 1, 256, 0, st, partials, (int)nb, (double)nf * nf * nf, 1, sc);
+  if (def && guard && fcells <= kTwoStepMaxFine) {
+    const int tpb = tpb_for(fcells);
+    launch_k(k_defect64, blocks_for(fcells, tpb), tpb, 0, st, nf, phi, src, f, c, def, guard);
+    launch_k(k_restrict_defects64, nb, 256, 0, st, nf, phi, (const double*)def,
+             (const unsigned char*)guard, phi_c, phihat_c, rd_c, partials);
+    count_launches(1);
+  } else {
+    launch_k(k_residual_restrict64, nb, 256, 0, st, nf, phi, src, f, c, phi_c, phihat_c, rd_c,
+             partials);
+  }
+  launch_k(k_finalize, 1, 256, 0, st, partials, (int)nb, (double)fcells, 1, sc);
   count_launches(2);
 }
 
@@ -260,15 +307,17 @@ void launch_fas_rhs64(cudaStream_t st, int nc, const double* phi_c, const double
                       double* f_c, const OpConst64& c, const LevelScalars* fine_sc,
                       LevelScalars* coarse_sc) {
   const long long cells = (long long)nc * nc * nc;
-  launch_k(k_fas_rhs64, blocks_for(cells, 256), 256, 0, st, nc, phi_c, src_c, f_c, c, fine_sc,
-                                                      coarse_sc);
+  const int tpb = tpb_for(cells);
+  launch_k(k_fas_rhs64, blocks_for(cells, tpb), tpb, 0, st, nc, phi_c, src_c, f_c, c, fine_sc,
+           coarse_sc);
   count_launches(1);
 }
 
 void launch_prolong_correct64(cudaStream_t st, int nc, const double* phi_c,
                               const double* phihat_c, double* phi_f) {
   const long long cells = 8LL * nc * nc * nc;
-  launch_k(k_prolong_correct64, blocks_for(cells, 256), 256, 0, st, nc, phi_c, phihat_c, phi_f);
+  const int tpb = tpb_for(cells);
+  launch_k(k_prolong_correct64, blocks_for(cells, tpb), tpb, 0, st, nc, phi_c, phihat_c, phi_f);
   count_launches(1);
 }
 

@@ -129,10 +129,17 @@ void launch_finalize(cudaStream_t st, const Partial* partials, int nparts, doubl
 void launch_residual64(cudaStream_t st, int n, const double* phi, const double* src,
                        const double* f, double* dout, const OpConst64& c, Partial* partials,
                        LevelScalars* sc, int periodic);
+// With def/guard (kTwoStepMaxFine entries) and nf^3 <= kTwoStepMaxFine, the
+// restriction runs as a per-fine-cell defect launch plus the coarse walk, so that
+// the FP64 work of a small level spreads over the GPU (same bits as the fused form).
 void launch_residual_restrict64(cudaStream_t st, int nf, const double* phi, const double* src,
                                 const double* f, const OpConst64& c, double* phi_c,
                                 double* phihat_c, double* rd_c, Partial* partials,
-                                LevelScalars* sc);
+                                LevelScalars* sc, double* def = nullptr,
+                                unsigned char* guard = nullptr);
+// Threads per block of a per-cell FP64 launch over `items` cells (256, or 64 on
+// small levels).
+int tpb_for(long long items);
 void launch_fas_rhs64(cudaStream_t st, int nc, const double* phi_c, const double* src_c,
                       double* f_c, const OpConst64& c, const LevelScalars* fine_sc,
                       LevelScalars* coarse_sc);
@@ -162,6 +169,10 @@ namespace mg {
 // sub-cycle at 32 slowed the six-solve 128^3 step by 3.5 % (FP64) and left the
 // mixed step unchanged)
 constexpr int kSubcycleMaxN = 16;
+// Fine levels up to this many cells restrict their residual in two launches
+// (32^3: the fused launch would put 16 blocks on 16 SMs).  The scratch of the
+// sub-cycle's residual step (kSubcycleMaxN^3 cells) shares the same buffer.
+constexpr long long kTwoStepMaxFine = 32768;
 constexpr int kSubcycleMaxLevels = 8;
 
 struct SubLevel64 {

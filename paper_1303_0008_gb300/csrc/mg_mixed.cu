@@ -103,6 +103,24 @@ __global__ void __launch_bounds__(256) k_residual_restrict32(
   b_residual_restrict32(nf, e, phi0, q0, g, c, e_c, ehat_c, rg_c, partials, blockIdx.x);
 }
 
+// The same in two launches for small levels (as k_defect64 and
+// k_restrict_defects64): per fine cell rho, then the walk over the children.
+__global__ void __launch_bounds__(256) k_defect32(int nf, const float* __restrict__ e,
+                                                  const float* __restrict__ phi0,
+                                                  const float* __restrict__ q0,
+                                                  const float* __restrict__ g, OpConst32 c,
+                                                  float* __restrict__ rout) {
+  PdlScope pdl_scope;
+  cell_defect32(nf, e, phi0, q0, g, c, rout, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(256) k_restrict_defects32(
+    int nf, const float* __restrict__ e, const float* __restrict__ rin, float* __restrict__ e_c,
+    float* __restrict__ ehat_c, float* __restrict__ rg_c, Partial* __restrict__ partials) {
+  PdlScope pdl_scope;
+  b_restrict_defects32(nf, e, rin, e_c, ehat_c, rg_c, partials, blockIdx.x);
+}
+
 // g^H = N^H(R e) - (R rho - mu^h); mu^H starts at 0.
 __global__ void __launch_bounds__(256) k_fas_rhs32(int nc, const float* __restrict__ e_c,
                                                    const float* __restrict__ phi0_c,
@@ -283,8 +301,19 @@ struct CycleMixed {
     Level& C = d->lv[l + 1];
     smooth(l, o->nu_pre);
     const unsigned nb = nblk(C.cells, 256);
-    launch_k(k_residual_restrict32, nb, 256, 0, st, L.n, L.e, L.phi0, L.q0, L.rhs, ops32[l], C.e,
-                                               C.ehat, C.rhs, d->d_part);
+    if (L.cells <= kTwoStepMaxFine) {
+      // small level: per-fine-cell defects spread over the GPU, then the walk over
+      // each coarse cell's children (the same bits as the fused kernel)
+      float* def = reinterpret_cast<float*>(d->d_subdef);
+      launch_k(k_defect32, nblk(L.cells, 64), 64, 0, st, L.n, L.e, L.phi0, L.q0, L.rhs, ops32[l],
+               def);
+      launch_k(k_restrict_defects32, nb, 256, 0, st, L.n, L.e, (const float*)def, C.e, C.ehat,
+               C.rhs, d->d_part);
+      count_launches(1);
+    } else {
+      launch_k(k_residual_restrict32, nb, 256, 0, st, L.n, L.e, L.phi0, L.q0, L.rhs, ops32[l], C.e,
+               C.ehat, C.rhs, d->d_part);
+    }
     launch_finalize(st, d->d_part, (int)nb, (double)L.cells, 1, sc32(l));
     launch_k(k_fas_rhs32, nblk(C.cells, 256), 256, 0, st, C.n, C.e, C.phi0, C.q0, C.rhs, ops32[l + 1],
                                                      sc32(l), sc32(l + 1));

@@ -38,8 +38,8 @@ struct Domain {
   LevelScalars* h_sc = nullptr;  // pinned mirror of d_sc[0] and d_sc[nlev]
   Partial* d_part = nullptr;
   int part_cap = 0;
-  // per-fine-cell defects and guard flags of the sub-cycle's residual step
-  // (kSubcycleMaxN^3 entries; the FP32 cycle stores floats in the same bytes)
+  // per-fine-cell defects and guard flags of the two-step residual restriction
+  // (kTwoStepMaxFine entries; the FP32 cycle stores floats in the same bytes)
   double* d_subdef = nullptr;
   unsigned char* d_subguard = nullptr;
   bool density_set = false;
