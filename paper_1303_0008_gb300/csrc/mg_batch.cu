@@ -171,10 +171,10 @@ __global__ void __launch_bounds__(256) kb_prolong32(const BItem* __restrict__ it
   b_prolong_correct32(it.n / 2, it.ce, it.cehat, it.e, blk);
 }
 
-__global__ void __launch_bounds__(256) kb_coarsest_corr64(const BItem* __restrict__ items,
+__global__ void __launch_bounds__(256) kb_coarsest_corr32(const BItem* __restrict__ items,
                                                           int sweeps, double drop) {
   const BItem& it = items[blockIdx.x];
-  b_coarsest_corr64(it.n, it.e, it.phi0, it.q0, it.rhs, it.op32, it.sc32, sweeps, drop, 0);
+  b_coarsest_corr32(it.n, it.e, it.phi0, it.q0, it.rhs, it.op32, it.sc32, sweeps, drop, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -436,7 +436,7 @@ struct BatchCycle {
     }
     const size_t smem = 4 * sizeof(double) * (size_t)bs->coarsest.maxn * bs->coarsest.maxn *
                         bs->coarsest.maxn;
-    kb_coarsest_corr64<<<bs->coarsest.count, 256, smem, st>>>(bs->coarsest.d, o->coarse_sweeps,
+    kb_coarsest_corr32<<<bs->coarsest.count, 256, smem, st>>>(bs->coarsest.d, o->coarse_sweeps,
                                                               o->coarse_drop);
     count_launches(1);
     for (int l = bs->lmax - 2; l >= 0; --l) {
@@ -480,7 +480,7 @@ mg_status batch_solve(mg_grid* g, const int* branch, const double* alpha, const 
   if (!attr) {
     cudaFuncSetAttribute(kb_coarsest64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          3 * sizeof(double) * 4096);
-    cudaFuncSetAttribute(kb_coarsest_corr64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(kb_coarsest_corr32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          4 * sizeof(double) * 4096);
     attr = true;
   }

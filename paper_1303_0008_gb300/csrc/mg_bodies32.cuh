@@ -6,30 +6,6 @@
 
 namespace mg {
 
-// The change of the root D when phi0 moves by e, from the stencils of e and
-// phi0, in FP64 with correctly rounded sqrt and division (the coarsest level of
-// the inner correction cycles): D(q1) - D(q0) = 2 sigma du / (sqrt q0 + sqrt q1)
-// where both discriminants are non-negative, k2 sigma (sqrt q1 - sqrt q0) of the
-// guarded roots otherwise.
-__device__ __forceinline__ double delta_D64(const StencilT<double>& se,
-                                            const StencilT<double>& sp, double q0, double g1,
-                                            double g2, double c3, double k2, double sigma) {
-  const double a1e = se.sx - se.sy, a2e = se.sx - se.sz, a3e = se.sy - se.sz;
-  const double a1p = sp.sx - sp.sy, a2p = sp.sx - sp.sz, a3p = sp.sy - sp.sz;
-  const double dA = a1e * (2.0 * a1p + a1e) + a2e * (2.0 * a2p + a2e) + a3e * (2.0 * a3p + a3e);
-  const double dB = se.cxy * (2.0 * sp.cxy + se.cxy) + se.cxz * (2.0 * sp.cxz + se.cxz) +
-                    se.cyz * (2.0 * sp.cyz + se.cyz);
-  const double du = g1 * dA + g2 * dB;
-  const double q1 = q0 + c3 * du;
-  const double s0 = sqrt(q0 > 0.0 ? q0 : 0.0);
-  const double s1 = sqrt(q1 > 0.0 ? q1 : 0.0);
-  if (q0 >= 0.0 && q1 >= 0.0) {
-    const double den = s0 + s1;
-    return den > 0.0 ? (sigma * 2.0 * du) / den : 0.0;
-  }
-  return sigma * k2 * (s1 - s0);
-}
-
 // The FP32 root change with every rounding spelled out (no contraction left to
 // the compiler), so that the per-colour kernels and the one-launch sweep, which
 // evaluates two cells per packed FP32x2 instruction, give the same bits.
@@ -493,20 +469,25 @@ __device__ __forceinline__ void b_prolong_correct32(int nc, const float* __restr
   cell_prolong32(nc, e_c, ehat_c, e_f, (long long)blk * blockDim.x + threadIdx.x);
 }
 
-__device__ __forceinline__ void b_coarsest_corr64(int n, float* __restrict__ e,
-                                                         const float* __restrict__ phi0,
-                                                         const float* __restrict__ q0,
-                                                         const float* __restrict__ g, OpConst32 c,
-                                                         LevelScalars* __restrict__ sc,
-                                                         int max_sweeps, double drop,
-    long long blk) {
-  extern __shared__ double smc[];
-  __shared__ double s_mu, s_res0, s_res;
+// The coarsest level of the inner correction cycle, in one CTA and in FP32 (the
+// precision of the inner problem): four-colour sweeps of the FP32 smoother's own
+// cell update until the residual falls by `drop`, stalls, reaches the FP32
+// rounding floor or `max_sweeps` is spent, with the residual checked every two
+// sweeps.  A single FP64 warp on 16 cells per colour (4^3) would take about 80
+// microseconds per visit on GB300's FP64 pipe; in FP32 it is a few.
+__device__ __forceinline__ void b_coarsest_corr32(int n, float* __restrict__ e,
+                                                  const float* __restrict__ phi0,
+                                                  const float* __restrict__ q0,
+                                                  const float* __restrict__ g, OpConst32 c,
+                                                  LevelScalars* __restrict__ sc, int max_sweeps,
+                                                  double drop, long long blk) {
+  extern __shared__ float smf[];
+  __shared__ double s_mu, s_res;
   const int cells = n * n * n;
-  double* se = smc;
-  double* sp = smc + cells;
-  double* sq = smc + 2 * cells;
-  double* sg = smc + 3 * cells;
+  float* se = smf;
+  float* sp = smf + cells;
+  float* sq = smf + 2 * cells;
+  float* sg = smf + 3 * cells;
   for (int q = threadIdx.x; q < cells; q += blockDim.x) {
     se[q] = e[q];
     sp[q] = phi0[q];
@@ -515,29 +496,24 @@ __device__ __forceinline__ void b_coarsest_corr64(int n, float* __restrict__ e,
   }
   if (threadIdx.x == 0) s_mu = sc->lambda;
   __syncthreads();
-  const double h2 = (double)c.h2, inv_h2 = (double)c.inv_h2;
-  const double g1 = (double)c.g1, g2 = (double)c.g2, c3 = (double)c.c3, k2 = (double)c.k2,
-               sigma = (double)c.sigma;
-  auto ddv = [&](const StencilT<double>& a, const StencilT<double>& b, double qq) {
-    if (c.linear) return 0.0;
-    return delta_D64(a, b, qq, g1, g2, c3, k2, sigma);
-  };
   double scale = 0.0;
+  // residual of N(e) = g + mu: mu = mean(N(e) - g), res = max |N(e) - g - mu|
   auto residual = [&]() {
     Partial p;
     partial_init(p);
-    double mag = 0.0;
+    float mag = 0.f;
     for (int q = threadIdx.x; q < cells; q += blockDim.x) {
-      const int i = q % n, j = (q / n) % n, k = q / (n * n);
-      const StencilT<double> a = gather_periodic<double>(se, i, j, k, n);
-      const StencilT<double> b = gather_periodic<double>(sp, i, j, k, n);
-      const double lnb = a.sx + a.sy + a.sz;
-      const double lap = lnb - 6.0 * se[q];
-      const double dd = ddv(a, b, sq[q]);
-      partial_add(p, fma(lap, inv_h2, -dd) - sg[q], false);
-      mag = fmax(mag, (fabs(lnb) + 6.0 * fabs(se[q])) * inv_h2 + fabs(dd) + fabs(sg[q]));
+      int i, j, k;
+      split3((unsigned)q, n, i, j, k);
+      const StencilT<float> a = gather_periodic(se, i, j, k, n);
+      float dd = 0.f;
+      if (!c.linear) dd = dD32(a, gather_periodic(sp, i, j, k, n), sq[q], c);
+      const float lnb = (a.sx + a.sy) + a.sz;
+      const float r = fmaf(lnb - 6.f * se[q], c.inv_h2, -dd) - sg[q];
+      partial_add(p, (double)r, false);
+      mag = fmaxf(mag, (fabsf(lnb) + 6.f * fabsf(se[q])) * c.inv_h2 + fabsf(dd) + fabsf(sg[q]));
     }
-    scale = block_max(mag);
+    scale = block_max((double)mag);
     p = block_reduce(p);
     if (threadIdx.x == 0) {
       const double mu = p.sum / (double)cells;
@@ -547,30 +523,29 @@ __device__ __forceinline__ void b_coarsest_corr64(int n, float* __restrict__ e,
     __syncthreads();
     return s_res;
   };
+  // FP32 unit roundoff: the floor below which the residual is rounding noise
+  auto done = [&](double r, double r0, double r_prev) {
+    if (!(r > drop * r0)) return true;
+    if (r <= 64.0 * 5.9604644775390625e-8 * scale) return true;
+    return r >= 0.95 * r_prev;
+  };
   const double r0 = residual();
   double r_prev = r0;
-  const int hn = n >> 1;
-  const int per_colour = hn * hn * n;
+  const int per_colour = (n >> 1) * (n >> 1) * n;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    const float mu = (float)s_mu;
     for (int colour = 0; colour < 4; ++colour) {
-      for (int t = threadIdx.x; t < per_colour; t += blockDim.x) {
-        const int m = t % hn, jj = (t / hn) % hn, k = t / (hn * hn);
-        const int i = 2 * m + ((colour ^ k) & 1);
-        const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
-        const int id = i + n * (j + n * k);
-        const StencilT<double> a = gather_periodic<double>(se, i, j, k, n);
-        const StencilT<double> b = gather_periodic<double>(sp, i, j, k, n);
-        se[id] = fma(-h2, ddv(a, b, sq[id]) + sg[id] + s_mu, a.sx + a.sy + a.sz) * (1.0 / 6.0);
-      }
+      for (int t = threadIdx.x; t < per_colour; t += blockDim.x)
+        cell_smooth32(n, se, sp, sq, sg, mu, c, colour, t);
       __syncthreads();
     }
     if ((sweep & 1) == 1 || sweep + 1 == max_sweeps) {
       const double r = residual();
-      if (coarsest_done(r, r0, r_prev, scale, drop)) break;
+      if (done(r, r0, r_prev)) break;
       r_prev = r;
     }
   }
-  for (int q = threadIdx.x; q < cells; q += blockDim.x) e[q] = (float)se[q];
+  for (int q = threadIdx.x; q < cells; q += blockDim.x) e[q] = se[q];
   if (threadIdx.x == 0) {
     sc->lambda = s_mu;
     sc->res = s_res;

@@ -139,16 +139,16 @@ __global__ void __launch_bounds__(256) k_prolong_correct32(int nc, const float* 
   b_prolong_correct32(nc, e_c, ehat_c, e_f, blockIdx.x);
 }
 
-// Coarsest inner level in one CTA, in FP64: sweeps of N(e) = g + mu until the
+// Coarsest inner level in one CTA, in FP32: sweeps of N(e) = g + mu until the
 // residual fell by `drop` or `max_sweeps`.
-__global__ void __launch_bounds__(256) k_coarsest_corr64(int n, float* __restrict__ e,
+__global__ void __launch_bounds__(256) k_coarsest_corr32(int n, float* __restrict__ e,
                                                          const float* __restrict__ phi0,
                                                          const float* __restrict__ q0,
                                                          const float* __restrict__ g, OpConst32 c,
                                                          LevelScalars* __restrict__ sc,
                                                          int max_sweeps, double drop) {
   PdlScope pdl_scope;
-  b_coarsest_corr64(n, e, phi0, q0, g, c, sc, max_sweeps, drop, blockIdx.x);
+  b_coarsest_corr32(n, e, phi0, q0, g, c, sc, max_sweeps, drop, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -214,7 +214,7 @@ static mg_status mixed_prepare(Domain* d) {
   }
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_coarsest_corr64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_coarsest_corr32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          4 * sizeof(double) * 4096);
     attr = true;
   }
@@ -293,7 +293,7 @@ struct CycleMixed {
     }
     if (l == d->nlev - 1) {
       const size_t smem = 4 * sizeof(double) * (size_t)L.cells;
-      launch_k(k_coarsest_corr64, 1, 256, smem, st, L.n, L.e, L.phi0, L.q0, L.rhs, ops32[l], sc32(l),
+      launch_k(k_coarsest_corr32, 1, 256, smem, st, L.n, L.e, L.phi0, L.q0, L.rhs, ops32[l], sc32(l),
                                               o->coarse_sweeps, o->coarse_drop);
       count_launches(1);
       return;

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) k_subcycle32(const __grid_constant__ SubC
   {
     const SubLevel32& B = a.lv32[a.nlev - 1];
     ph.blocks(1, [&](long long) {
-      b_coarsest_corr64(B.n, B.e, B.phi0, B.q0, B.rhs, B.op32, B.sc32, a.coarse_sweeps,
+      b_coarsest_corr32(B.n, B.e, B.phi0, B.q0, B.rhs, B.op32, B.sc32, a.coarse_sweeps,
                         a.coarse_drop, 0);
     });
   }
