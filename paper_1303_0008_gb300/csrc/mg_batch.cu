@@ -87,8 +87,10 @@ __global__ void __launch_bounds__(256) kb_finalize(const BItem* __restrict__ ite
                                                    int use32, int clear_mu) {
   const BItem& it = items[blockIdx.x];
   const long long cells = (long long)it.n * it.n * it.n;
+  // mode 0: restriction partials (one per 256 coarse cells); 1: one per 256
+  // cells; 2: the hand-off's, one per 256 kHandoffCells cells
   const long long work = mode == 0 ? cells / 8 : cells;
-  const int per = 256;
+  const int per = mode == 2 ? 256 * kHandoffCells : 256;
   const int nparts = (int)((work + per - 1) / per);
   LevelScalars* sc = use32 ? it.sc32 : it.sc;
   b_finalize(it.part, nparts, (double)cells, 1, sc, 0);
@@ -180,7 +182,8 @@ __global__ void __launch_bounds__(256) kb_coarsest_corr32(const BItem* __restric
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-enum ListType { T_SMOOTH = 0, T_RR, T_CELL, T_CCELL, T_ONE, T_NTYPES };
+// T_HAND: the outer residual hand-off, kHandoffCells cells per thread
+enum ListType { T_SMOOTH = 0, T_RR, T_CELL, T_CCELL, T_ONE, T_HAND, T_NTYPES };
 
 static long long blocks_of(ListType t, int n) {
   const long long cells = (long long)n * n * n;
@@ -189,6 +192,7 @@ static long long blocks_of(ListType t, int n) {
     case T_RR: return (cells / 8 + 255) / 256;
     case T_CELL: return (cells + 255) / 256;
     case T_CCELL: return (cells / 8 + 255) / 256;
+    case T_HAND: return (cells + 256 * kHandoffCells - 1) / (256 * kHandoffCells);
     default: return 1;
   }
 }
@@ -422,8 +426,8 @@ struct BatchCycle {
       for (int c = 0; c < 4; ++c) launch(L(l, T_SMOOTH, P_DESC), 256, kb_smooth32, c);
   }
   void part_a_mixed() const {
-    launch(L(0, T_CELL, P_HAS), 256, kb_handoff64);
-    finalize(0, T_CELL, 1, 0, 1);
+    launch(L(0, T_HAND, P_HAS), 256, kb_handoff64);
+    finalize(0, T_HAND, 2, 0, 1);
     cudaMemcpyAsync(bs->h_out, bs->d_out, sizeof(LevelScalars) * g->domains.size(),
                     cudaMemcpyDeviceToHost, st);
   }

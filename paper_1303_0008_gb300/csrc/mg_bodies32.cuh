@@ -80,16 +80,23 @@ __device__ __forceinline__ float2 dD2(const Stencil2& se, const Stencil2& sp, fl
   return make_float2(root_change32(q0.x, q1.x, du.x, c), root_change32(q0.y, q1.y, du.y, c));
 }
 
+// The FP64 residual of the outer defect correction and its hand-off to the FP32
+// inner problem.  Each thread takes kHandoffCells cells (a block covers
+// 256 kHandoffCells consecutive cells, coalesced per step), so the block's norm
+// reduction, about 15 FP64 warp instructions, is shared by several cells.
 __device__ __forceinline__ void b_residual_handoff64(
     int n, const double* __restrict__ phi, const double* __restrict__ src, OpConst64 c,
     const LevelScalars* __restrict__ sc, float* __restrict__ g, float* __restrict__ q0,
     float* __restrict__ phi0, float* __restrict__ e, Partial* __restrict__ partials,
     long long blk) {
   const long long cells = (long long)n * n * n;
-  const long long t = (long long)blk * blockDim.x + threadIdx.x;
   Partial p;
   partial_init(p);
-  if (t < cells) {
+  const double lam = sc->lambda;
+#pragma unroll 1
+  for (int r = 0; r < kHandoffCells; ++r) {
+    const long long t = ((long long)blk * kHandoffCells + r) * blockDim.x + threadIdx.x;
+    if (t >= cells) break;
     int i, j, k;
     split3((unsigned)t, n, i, j, k);
     const StencilT<double> s = gather_periodic(phi, i, j, k, n);
@@ -114,7 +121,7 @@ __device__ __forceinline__ void b_residual_handoff64(
     const double lap = (s.sx + s.sy + s.sz) - 6.0 * ctr;
     const double d = fma(lap, c.inv_h2, -D);
     partial_add(p, d, guard);
-    g[t] = (float)(sc->lambda - d);
+    g[t] = (float)(lam - d);
     q0[t] = (float)q;
     phi0[t] = (float)ctr;
     e[t] = 0.f;

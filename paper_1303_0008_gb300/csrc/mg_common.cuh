@@ -111,6 +111,9 @@ __device__ __forceinline__ long long lidx(int i, int j, int k, int n) {
   return (long long)i + (long long)n * ((long long)j + (long long)n * (long long)k);
 }
 
+// Cells per thread of the outer FP64 residual with its FP32 hand-off.
+constexpr int kHandoffCells = 4;
+
 // The 18 stencil neighbours of one cell in the form the operator uses.
 struct Stencil64 {
   double sx, sy, sz;     // face pair sums

@@ -326,7 +326,7 @@ struct CycleMixed {
   // FP64 residual, FP32 hand-off, convergence scalars to the host.
   void part_a() const {
     Level& L = d->lv[0];
-    const unsigned nb = nblk(L.cells, 256);
+    const unsigned nb = nblk(L.cells, 256 * kHandoffCells);
     launch_k(k_residual_handoff64, nb, 256, 0, st, L.n, L.phi, L.src, ops[0], d->d_sc, L.rhs, L.q0,
                                               L.phi0, L.e, d->d_part);
     count_launches(1);
