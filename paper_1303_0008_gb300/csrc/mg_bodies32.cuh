@@ -109,13 +109,13 @@ __device__ __forceinline__ void b_residual_handoff64(
       const double B = fma(s.cxy, s.cxy, fma(s.cxz, s.cxz, s.cyz * s.cyz));
       if (c.mode == OP_SQRT) {
         q = fma(c.e1h, A2, fma(c.e2, B, src[t]));
-        D = fma(c.k2s, sqrt_nonneg(q < 0.0 ? 0.0 : q), -c.k2);
+        D = fma(c.k2s, sqrt_clamped(q), -c.k2);
       } else {
         const double u = fma(c.c1h, A2, fma(c.c2, B, src[t]));
         q = fma(c.c3, u, 1.0);
         D = (q < 0.0) ? -c.k2 : (2.0 * u) / (1.0 + sqrt(q));
       }
-      guard = q < 0.0;
+      guard = neg_guard(q);
     }
     const double ctr = phi[t];
     const double lap = (s.sx + s.sy + s.sz) - 6.0 * ctr;

@@ -49,7 +49,7 @@ __device__ __forceinline__ void cell_smooth64(int n, double* __restrict__ phi,
   if (c.mode == OP_SQRT) {
     const double B = fma(s.cxy, s.cxy, fma(s.cxz, s.cxz, s.cyz * s.cyz));
     const double q = fma(c.e1h, half_A(s), fma(c.e2, B, src[id]));
-    v = fma(c.upd_s, sqrt_nonneg(q < 0.0 ? 0.0 : q), acc);
+    v = fma(c.upd_s, sqrt_clamped(q), acc);
   } else {
     bool g;
     v = fma(-c.h2_6, root_D(s, src[id], c, g), acc);

@@ -177,6 +177,27 @@ __device__ __forceinline__ double sqrt_nonneg(double q) {
   return (q == 0.0) ? 0.0 : q * rsqrt(q);
 }
 
+// sqrt_nonneg(q < 0 ? 0 : q) with both tests on the bit pattern (integer ALU
+// instructions instead of FP64 compares, which share GB300's narrow FP64 pipe).
+// As a signed 64-bit integer, +0 is 0 and the negative non-NaN doubles (-0 to
+// -inf) are exactly the values <= the pattern of -inf; negative NaNs lie above it
+// and, like every other input, take q * rsqrt(q).  Same result for every q.
+__device__ __forceinline__ double sqrt_clamped(double q) {
+  const long long b = __double_as_longlong(q);
+  return (b == 0 || b <= (long long)0xFFF0000000000000ULL) ? 0.0 : q * rsqrt(q);
+}
+
+// q < 0 on the bit pattern: the negative non-NaN doubles other than -0.
+__device__ __forceinline__ bool neg_guard(double q) {
+  const long long b = __double_as_longlong(q);
+  return b <= (long long)0xFFF0000000000000ULL && b != (long long)0x8000000000000000ULL;
+}
+
+// isfinite(d) on the bit pattern: the exponent field is not all ones.
+__device__ __forceinline__ bool finite_bits(double d) {
+  return ((__double_as_longlong(d) >> 52) & 0x7ff) != 0x7ff;
+}
+
 // D (the root of Eq. two_branch) from the stencil and the per-cell source term.
 // `guard` is set when the discriminant is negative.
 __device__ __forceinline__ double root_D(const StencilT<double>& s, double src,
@@ -189,8 +210,8 @@ __device__ __forceinline__ double root_D(const StencilT<double>& s, double src,
   const double B = fma(s.cxy, s.cxy, fma(s.cxz, s.cxz, s.cyz * s.cyz));
   if (c.mode == OP_SQRT) {
     const double q = fma(c.e1h, A2, fma(c.e2, B, src));
-    guard = q < 0.0;
-    return fma(c.k2s, sqrt_nonneg(guard ? 0.0 : q), -c.k2);
+    guard = neg_guard(q);
+    return fma(c.k2s, sqrt_clamped(q), -c.k2);
   }
   const double u = fma(c.c1h, A2, fma(c.c2, B, src));
   const double q = fma(c.c3, u, 1.0);
@@ -215,8 +236,8 @@ __device__ __forceinline__ double root_Dc(const StencilT<double>& s, double ctr,
                                           const OpConst64& c, bool& guard) {
   if (c.mode != OP_GENW) return root_D(s, src, c, guard);
   const double q = genw_q(s, ctr, src, c);
-  guard = q < 0.0;
-  return fma(c.k2s, sqrt_nonneg(guard ? 0.0 : q), -c.k2);
+  guard = neg_guard(q);
+  return fma(c.k2s, sqrt_clamped(q), -c.k2);
 }
 
 // Newton step of one cell for OP_GENW: phi - L/(dL/dphi) with
@@ -249,7 +270,7 @@ __device__ __forceinline__ void partial_init(Partial& p) {
 }
 
 __device__ __forceinline__ void partial_add(Partial& p, double d, bool guard) {
-  if (isfinite(d)) {
+  if (finite_bits(d)) {
     p.sum += d;
     p.dmax = fmax(p.dmax, d);
     p.dmin = fmin(p.dmin, d);
