@@ -39,7 +39,7 @@ __device__ __forceinline__ void cell_smooth64(int n, double* __restrict__ phi,
   if (c.mode == OP_GENW) {
     const double old = phi[id];
     const double v = genw_newton(s, old, src[id], (f ? f[id] : 0.0) + s_c, c);
-    phi[id] = c.omega != 1.0 ? fma(c.omega, v - old, old) : v;
+    phi[id] = not_one(c.omega) ? fma(c.omega, v - old, old) : v;
     return;
   }
   const double lapnb = s.sx + s.sy + s.sz;
@@ -54,7 +54,7 @@ __device__ __forceinline__ void cell_smooth64(int n, double* __restrict__ phi,
     bool g;
     v = fma(-c.h2_6, root_D(s, src[id], c, g), acc);
   }
-  if (c.omega != 1.0) {
+  if (not_one(c.omega)) {
     const double old = phi[id];
     v = fma(c.omega, v - old, old);
   }
@@ -337,7 +337,7 @@ __device__ __forceinline__ void b_coarsest64(int n, double* __restrict__ phi,
           const double D = root_D(s, ssrc[id], c, g);
           v = fma(-c.h2, D + sf[id] + s_lam, s.sx + s.sy + s.sz) * (1.0 / 6.0);
         }
-        sphi[id] = (c.omega != 1.0) ? fma(c.omega, v - sphi[id], sphi[id]) : v;
+        sphi[id] = not_one(c.omega) ? fma(c.omega, v - sphi[id], sphi[id]) : v;
       }
       __syncthreads();
     }

@@ -193,6 +193,11 @@ __device__ __forceinline__ bool neg_guard(double q) {
   return b <= (long long)0xFFF0000000000000ULL && b != (long long)0x8000000000000000ULL;
 }
 
+// x != 1.0 on the bit pattern (for the relaxation factor, validated in (0, 1]).
+__device__ __forceinline__ bool not_one(double x) {
+  return __double_as_longlong(x) != 0x3FF0000000000000LL;
+}
+
 // isfinite(d) on the bit pattern: the exponent field is not all ones.
 __device__ __forceinline__ bool finite_bits(double d) {
   return ((__double_as_longlong(d) >> 52) & 0x7ff) != 0x7ff;

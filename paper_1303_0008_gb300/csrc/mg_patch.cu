@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128) k_patch_smooth(double* __restrict__ phi,
     const double D = root_D(s, src[id], c, g);
     const double rhs = f ? f[id] : 0.0;
     const double v = fma(-c.h2, D + rhs, s.sx + s.sy + s.sz) * (1.0 / 6.0);
-    phi[id] = (c.omega != 1.0) ? fma(c.omega, v - tile_ctr<B>(tile, i, j, k),
+    phi[id] = not_one(c.omega) ? fma(c.omega, v - tile_ctr<B>(tile, i, j, k),
                                      tile_ctr<B>(tile, i, j, k))
                                : v;
   }
