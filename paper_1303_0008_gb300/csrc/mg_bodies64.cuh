@@ -260,6 +260,25 @@ __device__ __forceinline__ void cell_prolong64(int nc, const double* __restrict_
   phi_f[t] += v * (1.0 / 64.0);
 }
 
+// cell_prolong64 with the coarse correction phi_c - phihat_c already formed in
+// corr_c (the same subtractions, so the same bits).
+__device__ __forceinline__ void cell_prolong_corr64(int nc, const double* __restrict__ corr_c,
+                                                    double* __restrict__ phi_f, long long t) {
+  const int nf = nc << 1;
+  const long long cells = (long long)nf * nf * nf;
+  if (t >= cells) return;
+  int i, j, k;
+  split3((unsigned)t, nf, i, j, k);
+  const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+  const int I1 = (i & 1) ? wrap_up(I0, nc) : wrap_dn(I0, nc);
+  const int J1 = (j & 1) ? wrap_up(J0, nc) : wrap_dn(J0, nc);
+  const int K1 = (k & 1) ? wrap_up(K0, nc) : wrap_dn(K0, nc);
+  auto e = [&](int a, int b, int cc) { return corr_c[lidx(a, b, cc, nc)]; };
+  const double v = 27.0 * e(I0, J0, K0) + 9.0 * (e(I1, J0, K0) + e(I0, J1, K0) + e(I0, J0, K1)) +
+                   3.0 * (e(I1, J1, K0) + e(I1, J0, K1) + e(I0, J1, K1)) + e(I1, J1, K1);
+  phi_f[t] += v * (1.0 / 64.0);
+}
+
 __device__ __forceinline__ void b_prolong_correct64(int nc, const double* __restrict__ phi_c,
                                                            const double* __restrict__ phihat_c,
                                                            double* __restrict__ phi_f,

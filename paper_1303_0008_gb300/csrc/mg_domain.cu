@@ -186,7 +186,7 @@ struct Cycle64 {
                                d->d_part, sc, d->d_subdef, d->d_subguard);
     launch_fas_rhs64(st, C.n, C.phi, C.src, C.f, ops[l + 1], sc, d->d_sc + l + 1);
     descend(l + 1);
-    launch_prolong_correct64(st, C.n, C.phi, C.phihat, L.phi);
+    launch_prolong_correct64(st, C.n, C.phi, C.phihat, L.phi, true);
     launch_smooth64(st, L.n, L.phi, L.src, L.f, sc, ops[l], o->nu_post);
   }
 
@@ -214,7 +214,7 @@ struct Cycle64 {
     if (!(o->tau_stop > 0.0))  // else part_a computed it
       launch_fas_rhs64(st, C.n, C.phi, C.src, C.f, ops[1], d->d_sc, d->d_sc + 1);
     descend(1);
-    launch_prolong_correct64(st, C.n, C.phi, C.phihat, L.phi);
+    launch_prolong_correct64(st, C.n, C.phi, C.phihat, L.phi, true);
     launch_smooth64(st, L.n, L.phi, L.src, nullptr, d->d_sc, ops[0], o->nu_post, timer_b);
   }
 

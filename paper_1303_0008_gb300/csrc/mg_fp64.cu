@@ -88,6 +88,23 @@ __global__ void __launch_bounds__(256) k_restrict_defects64(
   b_restrict_defects64(nf, phi, din, gin, phi_c, phihat_c, rd_c, partials, blockIdx.x);
 }
 
+// The coarse correction phihat_c <- phi_c - phihat_c (R phi is not needed after
+// the prolongation), then the prolongation from it: the subtraction is done once
+// per coarse cell instead of once per fine cell that reads it.
+__global__ void __launch_bounds__(256) k_correction64(long long cells,
+                                                      const double* __restrict__ phi_c,
+                                                      double* __restrict__ phihat_c) {
+  PdlScope pdl_scope;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < cells) phihat_c[t] = phi_c[t] - phihat_c[t];
+}
+
+__global__ void __launch_bounds__(256) k_prolong_corr64(int nc, const double* __restrict__ corr_c,
+                                                        double* __restrict__ phi_f) {
+  PdlScope pdl_scope;
+  cell_prolong_corr64(nc, corr_c, phi_f, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // One block: reduce the partials in a fixed order and publish the scalars.
 __global__ void __launch_bounds__(256) k_finalize(const Partial* __restrict__ partials, int nparts,
                                                   double cells, int periodic,
@@ -314,8 +331,16 @@ void launch_fas_rhs64(cudaStream_t st, int nc, const double* phi_c, const double
 }
 
 void launch_prolong_correct64(cudaStream_t st, int nc, const double* phi_c,
-                              const double* phihat_c, double* phi_f) {
+                              const double* phihat_c, double* phi_f, bool clobber_hat) {
   const long long cells = 8LL * nc * nc * nc;
+  if (clobber_hat && cells >= kCorrectionMinFine) {
+    const long long cc = cells / 8;
+    double* corr = const_cast<double*>(phihat_c);
+    launch_k(k_correction64, blocks_for(cc, 256), 256, 0, st, cc, phi_c, corr);
+    launch_k(k_prolong_corr64, blocks_for(cells, 256), 256, 0, st, nc, (const double*)corr, phi_f);
+    count_launches(1);
+    return;
+  }
   const int tpb = tpb_for(cells);
   launch_k(k_prolong_correct64, blocks_for(cells, tpb), tpb, 0, st, nc, phi_c, phihat_c, phi_f);
   count_launches(1);

@@ -143,8 +143,12 @@ int tpb_for(long long items);
 void launch_fas_rhs64(cudaStream_t st, int nc, const double* phi_c, const double* src_c,
                       double* f_c, const OpConst64& c, const LevelScalars* fine_sc,
                       LevelScalars* coarse_sc);
+// clobber_hat: phihat_c may be overwritten (with phi_c - phihat_c); from
+// kCorrectionMinFine fine cells on, the correction is then formed once per coarse
+// cell before the prolongation (same bits).
+constexpr long long kCorrectionMinFine = 128LL * 128 * 128;
 void launch_prolong_correct64(cudaStream_t st, int nc, const double* phi_c,
-                              const double* phihat_c, double* phi_f);
+                              const double* phihat_c, double* phi_f, bool clobber_hat = false);
 void launch_coarsest64(cudaStream_t st, int n, double* phi, const double* src, const double* f,
                        const OpConst64& c, LevelScalars* sc, int max_sweeps, double drop);
 void launch_restrict64(cudaStream_t st, int nc, const double* fine, double* coarse);
