@@ -96,7 +96,10 @@ typedef struct {
                         1e-2: a tighter coarsest solve leaves the V-cycle count of the
                         128^3 lognormal solves unchanged and only costs time) */
   int time_kernels;  /* 1: time every launch of the finest-level smoother with CUDA
-                        events on the handle's stream (stats.kernel_ms); default 0 */
+                        events on the handle's stream (stats.kernel_ms); 2: time the
+                        first colour stage of each smoothing call only (an event
+                        between two launches removes their programmatic overlap, so
+                        this disturbs the solve less); default 0 */
   mg_guard guard;    /* default MG_GUARD_FLOOR */
   int patch_coarse_sweeps; /* sweeps on the coarsest (2^3 per patch) level of a
                               refinement union per V-cycle (default 8) */

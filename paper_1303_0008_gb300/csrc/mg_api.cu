@@ -55,6 +55,7 @@ void mg_default_options(mg_options* opt) {
 
 static mg_status check_options(const mg_options& o) {
   if (o.prec != MG_FP64 && o.prec != MG_MIXED) MG_FAIL(MG_EINVAL, "options: unknown precision");
+  if (o.time_kernels < 0 || o.time_kernels > 2) MG_FAIL(MG_EINVAL, "options: time_kernels must be 0, 1 or 2");
   if (o.nu_pre < 0 || o.nu_post < 0 || o.nu_pre + o.nu_post < 1 || o.nu_pre > 16 ||
       o.nu_post > 16)
     MG_FAIL(MG_EINVAL, "options: nu_pre/nu_post must be in [0,16] with a positive sum");

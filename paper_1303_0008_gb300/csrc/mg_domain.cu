@@ -306,6 +306,7 @@ mg_status domain_solve(Domain* d, const mg_options& o, cudaStream_t st, int bran
   } else {
     EventPairs ta, tb;
     ta.enabled = tb.enabled = o.time_kernels != 0;
+    ta.first_only = tb.first_only = o.time_kernels == 2;
     Cycle64 cyc{d, &o, st, ops.data(), &ta, &tb};
     domain_invalidate_graphs(d);
     const bool single = d->nlev == 1;

@@ -58,6 +58,7 @@ struct EventPairs {
   int n = 0;
   bool capturing = false;
   bool enabled = false;
+  bool first_only = false;  // time only the first colour stage of each smoothing call
   ~EventPairs() {
     for (auto e : start) cudaEventDestroy(e);
     for (auto e : stop) cudaEventDestroy(e);

@@ -308,6 +308,25 @@ def test_fused_coarse_subcycle_is_bit_identical(n):
     assert s1["launches"] < s2["launches"]
 
 
+@pytest.mark.gpu
+def test_kernel_timing_modes_leave_the_solve_unchanged():
+    """time_kernels = 1 brackets every finest-level colour stage with events, 2 only
+    the first of each smoothing call (2 sweeps x 4 colours -> 1); the solve is the
+    same bits in every mode."""
+    n = 32
+    delta = I.lognormal_delta(n, 1.5, 7)
+    a, _, s0 = gpu_solve(delta, 0.3, 1.0, tol=1e-10, time_kernels=0)
+    b, _, s1 = gpu_solve(delta, 0.3, 1.0, tol=1e-10, time_kernels=1)
+    c, _, s2 = gpu_solve(delta, 0.3, 1.0, tol=1e-10, time_kernels=2)
+    assert s0["rc"] == s1["rc"] == s2["rc"] == mg.MG_OK
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert s0["kernel_launches"] == 0
+    assert s1["kernel_launches"] == 8 * s2["kernel_launches"] > 0
+    assert s1["kernel_ms"] > 0 and s2["kernel_ms"] > 0
+    with pytest.raises(mg.MGError):
+        mg.mg_create_grid(n, mg.options(time_kernels=3))
+
+
 def test_errors_are_reported():
     n = 16
     with pytest.raises(mg.MGError) as e:
