@@ -322,7 +322,7 @@ __device__ __forceinline__ void b_residual_restrict32(
     // accuracy only), merged into the FP64 block partial once per thread
     float se_sum = 0.f, sr = 0.f, fsum = 0.f, fmx = -INFINITY, fmn = INFINITY;
     int bad = 0;
-#pragma unroll 1
+#pragma unroll 2
     for (int ch = 0; ch < 8; ++ch) {
       const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
       const long long id = lidx(i, j, k, nf);
