@@ -198,6 +198,58 @@ __device__ __forceinline__ void cell_smooth32(int n, float* __restrict__ e,
   e[id] = gs_value32(se, dd, g[id], mu, c);
 }
 
+// Face sums and cross differences around c0 for a side N known at compile time and
+// a cell off the y and z boundaries: cxp / cxm point at the x neighbours (the x
+// wrap is folded into them), so every load is a base pointer plus an immediate.
+// The sums are those of gather_at in the same order.
+template <int N>
+__device__ __forceinline__ StencilT<float> gather_n(const float* c0, const float* cxp,
+                                                    const float* cxm) {
+  constexpr int Y = N, Z = N * N;
+  StencilT<float> s;
+  s.sx = cxp[0] + cxm[0];
+  s.sy = c0[Y] + c0[-Y];
+  s.sz = c0[Z] + c0[-Z];
+  s.cxy = (cxp[Y] + cxm[-Y]) - (cxp[-Y] + cxm[Y]);
+  s.cxz = (cxp[Z] + cxm[-Z]) - (cxp[-Z] + cxm[Z]);
+  s.cyz = (c0[Y + Z] + c0[-Y - Z]) - (c0[Y - Z] + c0[-Y + Z]);
+  return s;
+}
+
+// cell_smooth32 for a side N known at compile time (N >= 64, so that a warp's 32
+// cells share their row, and the y/z-boundary test below is uniform per warp).
+// Rows on a y or z boundary take the general path; the others address their
+// neighbours with immediates.  The arithmetic is cell_smooth32's, so the bits are.
+template <int N>
+__device__ __forceinline__ void cell_smooth32_n(float* __restrict__ e,
+                                                const float* __restrict__ phi0,
+                                                const float* __restrict__ q0,
+                                                const float* __restrict__ g, float mu,
+                                                const OpConst32& c, int colour, long long t) {
+  static_assert(N >= 64 && (N & (N - 1)) == 0, "power of two, at least 64");
+  constexpr int HN = N / 2;
+  constexpr long long TOTAL = (long long)HN * HN * N;
+  if (t >= TOTAL) return;
+  const unsigned u = (unsigned)t;
+  const int m = (int)(u % HN), jj = (int)((u / HN) % HN), k = (int)(u / (HN * HN));
+  const int i = 2 * m + ((colour ^ k) & 1);
+  const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
+  if (j == 0 || j == N - 1 || k == 0 || k == N - 1) {
+    cell_smooth32(N, e, phi0, q0, g, mu, c, colour, t);
+    return;
+  }
+  const long long id = (long long)i + (long long)N * (j + (long long)N * k);
+  const int xp = (i == N - 1) ? 1 - N : 1, xm = (i == 0) ? N - 1 : -1;
+  const float* ce = e + id;
+  const StencilT<float> se = gather_n<N>(ce, ce + xp, ce + xm);
+  float dd = 0.f;
+  if (!c.linear) {
+    const float* cp = phi0 + id;
+    dd = dD32(se, gather_n<N>(cp, cp + xp, cp + xm), q0[id], c);
+  }
+  e[id] = gs_value32(se, dd, g[id], mu, c);
+}
+
 __device__ __forceinline__ void b_smooth_colour32(int n, float* __restrict__ e,
                                                          const float* __restrict__ phi0,
                                                          const float* __restrict__ q0,

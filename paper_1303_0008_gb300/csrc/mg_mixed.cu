@@ -82,6 +82,23 @@ __global__ void __launch_bounds__(256) k_smooth_colour32(int n, float* __restric
   b_smooth_colour32(n, e, phi0, q0, g, sc, c, colour, blockIdx.x);
 }
 
+// The same colour stage for a power-of-two side N >= 64 known at compile time
+// (immediate neighbour offsets; cell_smooth32_n).
+template <int N>
+__global__ void __launch_bounds__(256) k_smooth_colour32_n(float* __restrict__ e,
+                                                           const float* __restrict__ phi0,
+                                                           const float* __restrict__ q0,
+                                                           const float* __restrict__ g,
+                                                           const LevelScalars* __restrict__ sc,
+                                                           OpConst32 c, int colour) {
+  PdlScope pdl_scope;
+  __shared__ float s_mu;
+  if (threadIdx.x == 0) s_mu = (float)sc->lambda;
+  __syncthreads();
+  cell_smooth32_n<N>(e, phi0, q0, g, s_mu, c, colour,
+                     (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // The same colour stage with two cells of a row per thread (n % 4 == 0).
 __global__ void __launch_bounds__(256) k_smooth_colour32_pair(int n, float* __restrict__ e,
                                                               const float* __restrict__ phi0,
@@ -262,9 +279,34 @@ struct CycleMixed {
     }
     const long long per = (long long)(L.n / 2) * (L.n / 2) * L.n;
     for (int s = 0; s < sweeps; ++s)
-      for (int colour = 0; colour < 4; ++colour)
-        launch_k(k_smooth_colour32, nblk(per, 256), 256, 0, st, L.n, L.e, L.phi0, L.q0, L.rhs, sc32(l),
-                                                         ops32[l], colour);
+      for (int colour = 0; colour < 4; ++colour) {
+        const unsigned nb = nblk(per, 256);
+        switch (L.n) {
+          case 64:
+            launch_k(k_smooth_colour32_n<64>, nb, 256, 0, st, L.e, L.phi0, L.q0, L.rhs, sc32(l),
+                     ops32[l], colour);
+            break;
+          case 128:
+            launch_k(k_smooth_colour32_n<128>, nb, 256, 0, st, L.e, L.phi0, L.q0, L.rhs, sc32(l),
+                     ops32[l], colour);
+            break;
+          case 256:
+            launch_k(k_smooth_colour32_n<256>, nb, 256, 0, st, L.e, L.phi0, L.q0, L.rhs, sc32(l),
+                     ops32[l], colour);
+            break;
+          case 512:
+            launch_k(k_smooth_colour32_n<512>, nb, 256, 0, st, L.e, L.phi0, L.q0, L.rhs, sc32(l),
+                     ops32[l], colour);
+            break;
+          case 1024:
+            launch_k(k_smooth_colour32_n<1024>, nb, 256, 0, st, L.e, L.phi0, L.q0, L.rhs, sc32(l),
+                     ops32[l], colour);
+            break;
+          default:
+            launch_k(k_smooth_colour32, nb, 256, 0, st, L.n, L.e, L.phi0, L.q0, L.rhs, sc32(l),
+                     ops32[l], colour);
+        }
+      }
     count_launches(4LL * sweeps);
   }
 
