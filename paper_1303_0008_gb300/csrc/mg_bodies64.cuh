@@ -102,7 +102,14 @@ __device__ __forceinline__ void b_residual_restrict64(
   if (t < ccells) {
     int I, J, K;
     split3((unsigned)t, nc, I, J, K);
+    // The partial norms of the 8 children.  With every child finite, the sum is sd
+    // itself (the same additions in the same order) and the extremes are kept as
+    // integer order keys, so that the FP64 pipe, GB300's limit here, does only the
+    // two sums per child.  A non-finite child sends the coarse cell through the
+    // element-wise partial_add again (same values).
     double sphi = 0.0, sd = 0.0;
+    long long kmax = order_key(-INFINITY), kmin = order_key(INFINITY), guards = 0;
+    int bad = 0;
 #pragma unroll 1
     for (int ch = 0; ch < 8; ++ch) {
       const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
@@ -110,9 +117,28 @@ __device__ __forceinline__ void b_residual_restrict64(
       bool g;
       double ctr;
       const double d = fine_defect64(nf, phi, src, f, c, i, j, k, id, ctr, g);
-      partial_add(p, d, g);
+      const bool fin = finite_bits(d);
+      const long long key = order_key(d);
+      kmax = (fin && key > kmax) ? key : kmax;
+      kmin = (fin && key < kmin) ? key : kmin;
+      bad += fin ? 0 : 1;
+      guards += g ? 1 : 0;
       sphi += ctr;
       sd += d;
+    }
+    if (bad == 0) {
+      p.sum = sd;
+      p.dmax = from_order_key(kmax);
+      p.dmin = from_order_key(kmin);
+      p.guards = guards;
+    } else {
+#pragma unroll 1
+      for (int ch = 0; ch < 8; ++ch) {
+        const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
+        bool g;
+        double ctr;
+        partial_add(p, fine_defect64(nf, phi, src, f, c, i, j, k, lidx(i, j, k, nf), ctr, g), g);
+      }
     }
     phi_c[t] = sphi * 0.125;
     phihat_c[t] = sphi * 0.125;

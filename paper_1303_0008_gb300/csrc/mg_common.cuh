@@ -198,6 +198,17 @@ __device__ __forceinline__ bool not_one(double x) {
   return __double_as_longlong(x) != 0x3FF0000000000000LL;
 }
 
+// An integer key of a double whose order is the numeric order (-0 below +0): the
+// bit pattern with the magnitude bits flipped for negative values.  The map is
+// its own inverse.
+__device__ __forceinline__ long long order_key(double d) {
+  const long long b = __double_as_longlong(d);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ double from_order_key(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFLL));
+}
+
 // isfinite(d) on the bit pattern: the exponent field is not all ones.
 __device__ __forceinline__ bool finite_bits(double d) {
   return ((__double_as_longlong(d) >> 52) & 0x7ff) != 0x7ff;
