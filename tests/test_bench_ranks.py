@@ -44,3 +44,22 @@ def test_max_and_sum_over_two_gloo_ranks():
 def test_single_process_aggregation_is_identity():
     import bench
     assert bench.max_over_ranks(3.5) == 3.5 and bench.sum_over_ranks(6.0) == 6.0
+
+
+def test_traffic_record_matches_the_smoother_source():
+    """The benchmark's DRAM-traffic figure is tied to a hash of the finest-level
+    smoother's source (both headers of its body, the kernel, its launcher and the
+    block-size rule).  The three definitions must still be found, and the committed
+    record must carry the current hash, else the benchmark reports no traffic."""
+    import json
+    import bench
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    csrc = os.path.join(root, "paper_1303_0008_gb300", "csrc", "mg_fp64.cu")
+    text = open(csrc).read()
+    for head in ("__global__ void __launch_bounds__(256) k_smooth_colour64(",
+                 "int tpb_for(long long items)", "void launch_smooth64("):
+        part = bench._definition(text, head)
+        assert part.startswith(head) and part.rstrip().endswith("}")
+    rec = json.load(open(os.path.join(root, "profiles", "traffic.json")))["k_smooth_colour64"]
+    assert rec["source_hash"] == bench.kernel_source_hash()
+    assert bench.traffic_per_launch("k_smooth_colour64") == rec["bytes_per_launch_full_size"] > 0
