@@ -56,3 +56,7 @@ def test_binding_rejects_bad_arguments_without_gpu(libpath):
     assert e.value.status == mg.MG_EINVAL
     with pytest.raises(mg.MGError):
         mg.options(nu_pre=0, nu_post=0) and mg.mg_create_grid(8, mg.options(nu_pre=0, nu_post=0))
+    for bad in (dict(time_kernels=3), dict(time_kernels=-1), dict(omega=1.5), dict(coarse_sweeps=0)):
+        with pytest.raises(mg.MGError) as e:
+            mg.mg_create_grid(8, mg.options(**bad))
+        assert e.value.status == mg.MG_EINVAL, bad
