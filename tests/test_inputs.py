@@ -78,3 +78,38 @@ def test_batch_workload_ranges():
     for s in b:
         assert 0.5 <= s["sigma"] <= 2.5 and 2.0 <= s["r_v"] <= 16.0
         assert s["alpha"] == pytest.approx(math.copysign(I.alpha_kappa_for_rv(s["r_v"]), s["kappa"]))
+
+
+@pytest.mark.parametrize("n0,sigma,thr", [(16, 2.0, (15.0, 40.0)), (32, 2.0, (20.0, 80.0))])
+def test_refined_hierarchy_patches_are_aligned_unique_and_properly_nested(n0, sigma, thr):
+    """Patch origins are multiples of 8 inside their level's periodic index space,
+    each appears once, and every level-2 patch's parent block, dilated by one
+    level-1 cell (the trilinear ghost stencil of Sec. III.C), lies inside level-1
+    patches.  The densities are contrasts of a positive density."""
+    h = I.refined_hierarchy(n0, sigma, 5, thresholds=thr)
+    assert all(L["origins"].shape[0] > 0 for L in h["levels"])   # both levels exercised
+    n = n0
+    covered = None
+    for lvl, L in enumerate(h["levels"], start=1):
+        n *= 2
+        org = L["origins"]
+        if org.shape[0] == 0:
+            continue
+        assert org.dtype == np.int32 and (org % I.PATCH == 0).all()
+        assert (org >= 0).all() and (org < n).all()
+        assert len({tuple(o) for o in org}) == org.shape[0]
+        assert L["delta"].shape == (org.shape[0], 8, 8, 8) and L["delta"].min() > -1.0
+        if lvl == 2:
+            n1 = n // 2
+            for o in org:
+                par = o // 2
+                for dz in range(-1, 5):
+                    for dy in range(-1, 5):
+                        for dx in range(-1, 5):
+                            c = ((par[0] + dx) % n1, (par[1] + dy) % n1, (par[2] + dz) % n1)
+                            assert (c[0] // 8, c[1] // 8, c[2] // 8) in covered
+        covered = {tuple(o // I.PATCH) for o in org}
+    h2 = I.refined_hierarchy(n0, sigma, 5, thresholds=thr)
+    assert np.array_equal(h["delta0"], h2["delta0"])
+    for a, b in zip(h["levels"], h2["levels"]):
+        assert np.array_equal(a["origins"], b["origins"]) and np.array_equal(a["delta"], b["delta"])
