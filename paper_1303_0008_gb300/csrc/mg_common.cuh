@@ -114,12 +114,9 @@ __device__ __forceinline__ long long lidx(int i, int j, int k, int n) {
 // Cells per thread of the outer FP64 residual with its FP32 hand-off.
 constexpr int kHandoffCells = 4;
 
-// The 18 stencil neighbours of one cell in the form the operator uses.
-struct Stencil64 {
-  double sx, sy, sz;     // face pair sums
-  double cxy, cxz, cyz;  // cross differences (without the 1/4)
-};
 
+// The 18 stencil neighbours of one cell in the form the operator uses: face pair
+// sums and cross differences (without the 1/4).
 template <typename T>
 struct StencilT {
   T sx, sy, sz, cxy, cxz, cyz;
@@ -285,11 +282,14 @@ __device__ __forceinline__ void partial_init(Partial& p) {
   p.nonfinite = 0;
 }
 
+// The extremes compare integer order keys (order_key) rather than FP64 values:
+// the FP64 pipe is the limit of the kernels that call this per cell.
 __device__ __forceinline__ void partial_add(Partial& p, double d, bool guard) {
   if (finite_bits(d)) {
     p.sum += d;
-    p.dmax = fmax(p.dmax, d);
-    p.dmin = fmin(p.dmin, d);
+    const long long k = order_key(d);
+    if (k > order_key(p.dmax)) p.dmax = d;
+    if (k < order_key(p.dmin)) p.dmin = d;
   } else {
     p.nonfinite += 1;
   }
