@@ -60,3 +60,51 @@ def test_binding_rejects_bad_arguments_without_gpu(libpath):
         with pytest.raises(mg.MGError) as e:
             mg.mg_create_grid(8, mg.options(**bad))
         assert e.value.status == mg.MG_EINVAL, bad
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and offsetof of a header struct, from a C program built with the
+    host compiler against include/mg.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mg.h"', 'int main(void) {',
+             f'  printf("%zu\\n", sizeof({struct}));']
+    lines += [f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ['  return 0;', '}']
+    src = tmp_path / f"{struct}.c"
+    exe = tmp_path / f"{struct}.out"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run([cc, "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("name", ["mg_options", "mg_solve_stats"])
+def test_binding_structs_match_the_header_layout(name, tmp_path):
+    """The ctypes mirrors of the header's option and statistics structs have the
+    header's size and every field at the header's offset."""
+    from paper_1303_0008_gb300 import mg
+    cls = getattr(mg, name)
+    fields = [f for f, _ in cls._fields_]
+    # Python keywords carry a trailing underscore in the binding (lambda_)
+    size, offsets = _c_layout(name, [f.rstrip("_") for f in fields], tmp_path)
+    assert ctypes_sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offsets
+
+
+def ctypes_sizeof(cls):
+    import ctypes
+    return ctypes.sizeof(cls)
+
+
+def test_default_options_are_the_documented_ones(libpath):
+    """mg_default_options (a host call) fills the documented defaults."""
+    from paper_1303_0008_gb300 import mg
+    o = mg.options()
+    assert (o.prec, o.nu_pre, o.nu_post) == (mg.MG_FP64, 2, 2)
+    assert (o.coarse_sweeps, o.coarse_drop, o.time_kernels) == (4, 1e-2, 0)
+    assert o.omega == 1.0 and abs(o.w - 1.0 / 3.0) < 1e-15
