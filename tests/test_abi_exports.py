@@ -108,3 +108,29 @@ def test_default_options_are_the_documented_ones(libpath):
     assert (o.prec, o.nu_pre, o.nu_post) == (mg.MG_FP64, 2, 2)
     assert (o.coarse_sweeps, o.coarse_drop, o.time_kernels) == (4, 1e-2, 0)
     assert o.omega == 1.0 and abs(o.w - 1.0 / 3.0) < 1e-15
+
+
+def test_product_package_never_reaches_the_oracle():
+    """The product path (the package's modules and its CUDA sources) imports, loads
+    or builds nothing from oracle/: the oracle is test infrastructure only, and the
+    binding fails loudly instead of falling back to it."""
+    import ast
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_1303_0008_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath:
+            continue
+        for fn in files:
+            path = os.path.join(dirpath, fn)
+            if fn.endswith(".py"):
+                tree = ast.parse(open(path).read())
+                for node in ast.walk(tree):
+                    if isinstance(node, ast.Import):
+                        assert not any(a.name.split(".")[0] == "oracle" for a in node.names), path
+                    if isinstance(node, ast.ImportFrom):
+                        assert (node.module or "").split(".")[0] != "oracle", path
+                    if isinstance(node, ast.Constant) and isinstance(node.value, str):
+                        assert "liborc" not in node.value and "mg_oracle" not in node.value, path
+            elif fn.endswith((".cu", ".cuh", ".h")):
+                text = open(path).read()
+                assert "oracle/" not in text and "mg_oracle" not in text, path
