@@ -99,7 +99,9 @@ typedef struct {
                         events on the handle's stream (stats.kernel_ms); 2: time the
                         first colour stage of each smoothing call only (an event
                         between two launches removes their programmatic overlap, so
-                        this disturbs the solve less); default 0 */
+                        this disturbs the solve less); default 0.  With MG_MIXED the
+                        timed launches are the finest level's FP32 colour stages (not
+                        timed with sweep32 or pair32). */
   mg_guard guard;    /* default MG_GUARD_FLOOR */
   int patch_coarse_sweeps; /* sweeps on the coarsest (2^3 per patch) level of a
                               refinement union per V-cycle (default 8) */

@@ -73,6 +73,27 @@ def lib():
     return _LIB
 
 
+_LIBC = None
+
+
+def lib_colour():
+    """The four-colour OpenMP build of the oracle (liboracle_colour.so)."""
+    global _LIBC
+    if _LIBC is None:
+        L = ctypes.CDLL(build_oracle.build_colour())
+        L.orc_fas_solve_colour.restype = ctypes.c_int
+        L.orc_fas_solve_colour.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.orc_colour_sweeps.restype = ctypes.c_int
+        L.orc_colour_sweeps.argtypes = [ctypes.c_int, _D, _D, _D, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_int, ctypes.c_int]
+        _LIBC = L
+    return _LIBC
+
+
 def _f64(a):
     a = np.ascontiguousarray(a, dtype=np.float64)
     return a
@@ -159,6 +180,35 @@ def fas_solve(delta, alpha, kappa, branch=0, tol=1e-10, phi0=None, max_cycles=10
     return phi, {"status": int(st), "cycles": cyc, "res": float(stats[1]),
                  "lambda": float(stats[2]), "guard_hits": int(stats[3]),
                  "res0": float(stats[5]), "hist": stats[6:6 + cyc].copy()}
+
+
+def fas_solve_colour(delta, alpha, kappa, branch=0, tol=1e-10, phi0=None, max_cycles=100,
+                     nu_pre=2, nu_post=2, coarsest=4, w=W_PAPER, threads=0):
+    """fas_solve with four-colour sweeps on `threads` OpenMP threads (0: all cores).
+    Returns (phi (zero mean), stats dict with "threads")."""
+    delta = _f64(delta)
+    phi = np.zeros_like(delta) if phi0 is None else _f64(phi0).copy()
+    stats = np.zeros(7 + max(max_cycles, 1))
+    st = lib_colour().orc_fas_solve_colour(delta.shape[0], _p(delta), _p(phi), alpha, kappa,
+                                           branch, w, tol, max_cycles, nu_pre, nu_post,
+                                           coarsest, threads, _p(stats))
+    cyc = int(stats[0])
+    return phi, {"status": int(st), "cycles": cyc, "res": float(stats[1]),
+                 "lambda": float(stats[2]), "guard_hits": int(stats[3]),
+                 "res0": float(stats[5]), "hist": stats[6:6 + cyc].copy(),
+                 "threads": int(stats[6 + max_cycles])}
+
+
+def colour_sweeps(phi, delta, alpha, kappa, branch=0, f=None, lam=0.0, sweeps=1, w=W_PAPER,
+                  threads=0):
+    """Four-colour Newton-Gauss-Seidel sweeps of L^h phi = f + lam in place on a copy;
+    returns (phi, threads used)."""
+    phi = _f64(phi).copy()
+    delta = _f64(delta)
+    f = None if f is None else _f64(f)
+    t = lib_colour().orc_colour_sweeps(phi.shape[0], _p(phi), _p(delta), _p(f), lam, alpha,
+                                       kappa, branch, w, sweeps, threads)
+    return phi, int(t)
 
 
 def _parent_args(level, parent, parent_org):

@@ -250,6 +250,7 @@ struct CycleMixed {
   const OpConst32* ops32;
   float kappa;
   int floor;
+  EventPairs* timer;  // finest-level colour stages (time_kernels), or null
 
   LevelScalars* sc32(int l) const { return d->d_sc + d->nlev + l; }
 
@@ -278,9 +279,14 @@ struct CycleMixed {
       return;
     }
     const long long per = (long long)(L.n / 2) * (L.n / 2) * L.n;
+    EventPairs* t = (l == 0 && timer && timer->enabled) ? timer : nullptr;
     for (int s = 0; s < sweeps; ++s)
       for (int colour = 0; colour < 4; ++colour) {
         const unsigned nb = nblk(per, 256);
+        // an event between two launches removes their programmatic overlap, so the
+        // sampled mode brackets one colour stage per call
+        const bool timed = t && (!t->first_only || (s == 0 && colour == 0));
+        if (timed) t->begin(st);
         switch (L.n) {
           case 64:
             launch_k(k_smooth_colour32_n<64>, nb, 256, 0, st, L.e, L.phi0, L.q0, L.rhs, sc32(l),
@@ -306,6 +312,7 @@ struct CycleMixed {
             launch_k(k_smooth_colour32, nb, 256, 0, st, L.n, L.e, L.phi0, L.q0, L.rhs, sc32(l),
                      ops32[l], colour);
         }
+        if (timed) t->end(st);
       }
     count_launches(4LL * sweeps);
   }
@@ -400,14 +407,34 @@ mg_status mixed_solve(Domain* d, const mg_options& o, cudaStream_t st, const OpC
   if (ps != MG_OK) return ps;
   std::vector<OpConst32> ops32(d->nlev);
   for (int l = 0; l < d->nlev; ++l) ops32[l] = make_op32(d->lv[l].n, alpha, branch);
-  CycleMixed cyc{d, &o, st, ops, ops32.data(), (float)kappa, o.guard == MG_GUARD_FLOOR};
+  // the finest FP32 colour stages are timed when they run as per-colour launches
+  EventPairs tb;
+  tb.enabled = o.time_kernels != 0 && !o.sweep32 && !o.pair32;
+  tb.first_only = o.time_kernels == 2;
+  CycleMixed cyc{d, &o, st, ops, ops32.data(), (float)kappa, o.guard == MG_GUARD_FLOOR, &tb};
   domain_invalidate_graphs(d);
   long long na = 0, nb = 0;
   if (o.use_graphs) {
+    tb.capturing = true;
     d->gexec[2] = capture_graph(st, &na, [&] { cyc.part_a(); });
     d->gexec[3] = capture_graph(st, &nb, [&] { cyc.part_b(); });
+    tb.capturing = false;
   }
   const bool graphs = o.use_graphs && d->gexec[2] && d->gexec[3];
+  const int pairs_b = tb.n;
+  const double cells_per_launch = (double)d->lv[0].cells / 4.0;
+  bool b_pending = false;
+  auto harvest = [&]() {
+    if (!tb.enabled || !b_pending) return;
+    const int pairs = graphs ? pairs_b : tb.n;
+    const int keep = tb.n;
+    tb.n = pairs;
+    s->kernel_ms += tb.read_ms();
+    s->kernel_launches += pairs;
+    s->kernel_cells += pairs * cells_per_launch;
+    tb.n = keep;
+    b_pending = false;
+  };
   double first = -1.0;
   std::vector<double> hist;
   mg_status result = MG_OK;
@@ -420,6 +447,7 @@ mg_status mixed_solve(Domain* d, const mg_options& o, cudaStream_t st, const OpC
     }
     MCK(cudaStreamSynchronize(st));
     MCK(cudaGetLastError());
+    harvest();
     const double res = d->h_sc[0].res;
     s->outer += 1;
     s->guard_hits = o.guard == MG_GUARD_FLOOR ? (long long)d->h_sc[0].floored
@@ -451,12 +479,14 @@ mg_status mixed_solve(Domain* d, const mg_options& o, cudaStream_t st, const OpC
       result = MG_ENOCONV;
       break;
     }
+    if (!graphs) tb.n = 0;
     if (graphs) {
       MCK(cudaGraphLaunch(d->gexec[3], st));
       tl_launches += nb;
     } else {
       cyc.part_b();
     }
+    b_pending = true;
     s->cycles += o.inner_cycles;
   }
   s->res0 = first;
