@@ -1,18 +1,19 @@
 """Benchmark of the DGP scalar-field FAS solver on one GB300 per rank.
 
-Workload: the 128^3 periodic lognormal field (sigma = 1.5, P(k) ~ k^-2, seed
-1302) with six (alpha, kappa) pairs: Vainshtein radius 2, 8 and 32 cells, each
-with the sign of alpha (and kappa) flipped.  One step solves all six from a zero
-initial guess to max|d - lambda| < 1e-8 with the FP64 path; `value` is solves
-per second over all ranks (each rank solves its own copy: weak scaling, no
-collective on the data path).  The mixed-precision path is timed on the same
-workload and reported under "mixed".
+Workload: the 512^3 periodic lognormal field (sigma 2.0, P(k) ~ k^-2, seed 1304),
+normal branch, alpha*kappa = 2.4 (Vainshtein radius 16 cells of the reference
+top-hat), solved from phi = 0 to max|d - lambda| < 1e-8.  One step is one solve.
+`value` is FP64 solves per second over all ranks (each rank solves its own copy:
+weak scaling, no collective on the data path); the mixed-precision path (FP32
+correction cycles inside FP64 defect correction) is timed on the same workload
+and reported under "mixed".  The 128^3 six-solve workload (sigma 1.5, seed 1302,
+r_V = 2, 8, 32 cells, both signs) is reported under "secondary".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-`--impl reference` times the CPU oracle (one of the six solves per step, cycling)
-on the host cores of rank 0 and prints the same JSON line with "impl":
-"reference".
+`--impl reference` times the CPU oracle's four-colour OpenMP build on the host
+cores of rank 0 (a bounded sample of each solve, scaled to solves/s) and prints
+the same JSON line with "impl": "reference".
 """
 from __future__ import annotations
 
@@ -33,21 +34,36 @@ if ROOT not in sys.path:
 
 METRIC = ("smoother cell-updates/s & FAS solves/s to residual 1e-8 (FP64 vs mixed), "
           "% HBM roofline")
-N = 128
-SIGMA = 1.5
-SEED = 1302
+N = 512
+SIGMA = 2.0
+SEED = 1304
+R_V = 16.0
 TOL = 1e-8
+WORKLOAD = ("512^3 periodic lognormal delta (sigma 2.0, P(k)~k^-2, seed 1304), normal branch, "
+            "alpha*kappa = 2.4 (r_V = 16 cells), max|d - lambda| < 1e-8 from phi = 0; "
+            "FP64 vs mixed precision")
 # FP64 operations of one smoother cell update (FMA counted as 2, sqrt as 1): face
 # sums 3, Sigma_d 22 (A: 3 differences + 5; B: 9 cross-difference sums + 5),
 # q 4, sqrt 1, root 2, update 6.
 FLOP_PER_CELL_FP64 = 38
+# bytes of one FP32 correction-smoother cell update: e, phi0, q0 and g read, e written
+BYTES_PER_CELL_FP32 = 20
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070   # SMs x DFMA/clk x flop/DFMA x max GHz
+HBM_FALLBACK_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
+# the secondary workload
+N2, SIGMA2, SEED2 = 128, 1.5, 1302
 
 
 def workload():
     from paper_1303_0008_gb300 import inputs
-    return inputs.workload_lognormal_sweep(N, SIGMA, SEED)
+    return {"delta": inputs.lognormal_delta(N, SIGMA, SEED),
+            "alpha": inputs.alpha_kappa_for_rv(R_V), "kappa": 1.0, "branch": 0}
+
+
+def workload_secondary():
+    from paper_1303_0008_gb300 import inputs
+    return inputs.workload_lognormal_sweep(N2, SIGMA2, SEED2)
 
 
 def world():
@@ -152,34 +168,53 @@ def _definition(text: str, head: str) -> str:
     return text[i:]
 
 
-def kernel_source_hash():
-    """Hash of the source that defines the finest-level smoother and its launch: the
-    two headers its body comes from, plus the kernel, its launcher and the block-size
-    rule in mg_fp64.cu (other kernels in that file do not change it)."""
+# source that determines each roofline kernel's traffic: the headers of its body
+# and the definitions (kernel, launcher, block-size rule) in its translation unit
+_KERNEL_SOURCES = {
+    "k_smooth_colour64": (("mg_bodies64.cuh", "mg_common.cuh"), "mg_fp64.cu",
+                          ("__global__ void __launch_bounds__(256) k_smooth_colour64(",
+                           "int tpb_for(long long items)", "void launch_smooth64(")),
+    "k_smooth_colour32_n": (("mg_bodies32.cuh", "mg_common.cuh"), "mg_mixed.cu",
+                            ("__global__ void __launch_bounds__(256) k_smooth_colour32_n(",
+                             "  void smooth(int l, int sweeps) const {")),
+}
+
+
+def kernel_source_hash(kernel: str = "k_smooth_colour64"):
+    """Hash of the source that defines `kernel` and its launch: the headers its body
+    comes from, plus the kernel and its launcher in its translation unit (other
+    kernels in that file do not change it)."""
+    headers, unit, heads = _KERNEL_SOURCES[kernel]
     csrc = os.path.join(ROOT, "paper_1303_0008_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("mg_bodies64.cuh", "mg_common.cuh"):
+    for f in headers:
         h.update(open(os.path.join(csrc, f), "rb").read())
-    fp64 = open(os.path.join(csrc, "mg_fp64.cu")).read()
-    for head in ("__global__ void __launch_bounds__(256) k_smooth_colour64(",
-                 "int tpb_for(long long items)", "void launch_smooth64("):
-        part = _definition(fp64, head)
+    text = open(os.path.join(csrc, unit)).read()
+    for head in heads:
+        part = _definition(text, head)
         assert part, head
         h.update(part.encode())
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+def traffic_per_launch(kernel: str, cells_per_launch: float):
+    """DRAM bytes per launch of `kernel` at `cells_per_launch` cell updates, from the
+    committed ncu record, if it was taken on the current kernel source (else None).
+    The record was taken on a grid whose arrays exceed L2, so the traffic grows in
+    proportion to the cells a launch updates."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    data = json.load(open(path))
-    ent = data.get(kernel)
-    if not ent or ent.get("source_hash") != kernel_source_hash():
+    ent = json.load(open(path)).get(kernel)
+    if (not ent or ent.get("source_hash") != kernel_source_hash(kernel) or
+            not ent.get("bytes_per_launch") or not ent.get("cells_per_launch")):
         return None
-    return ent.get("bytes_per_launch_full_size")
+    return ent["bytes_per_launch"] * cells_per_launch / ent["cells_per_launch"]
+
+
+def _peaks():
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(pk)) if os.path.exists(pk) else {}
 
 
 def run_ours(args):
@@ -197,74 +232,120 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     w = workload()
     delta_np = w["delta"]
-    solves = w["solves"]
     delta = torch.from_numpy(delta_np).cuda()
     zero = torch.zeros_like(delta)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    def make(prec, time_kernels):
-        g = mg.mg_create_grid(N, mg.options(prec=prec, time_kernels=time_kernels))
+    def make(prec, time_kernels, n=N, dev=delta):
+        g = mg.mg_create_grid(n, mg.options(prec=prec, time_kernels=time_kernels))
         mg.mg_set_stream(g, stream)
-        mg.mg_set_density(g, 0, -1, delta)
+        mg.mg_set_density(g, 0, -1, dev)
         return g
 
-    def step(g, stats_out):
-        for s in solves:
-            mg.mg_set_field(g, 0, -1, zero)
-            st = mg.mg_solve(g, s["branch"], s["alpha"], s["kappa"], TOL)
-            stats_out.append(st)
-
-    def timed(g, steps, warmup):
-        for _ in range(warmup):
-            step(g, [])
+    def barrier():
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        per_step = []
-        stats = []
+
+    def timed(step, steps, warmup):
+        for _ in range(warmup):
+            step([])
+        barrier()
+        per_step, stats = [], []
         for _ in range(steps):
             flush.zero_()                     # L2 flush: write a buffer larger than L2
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(g, stats)
+            step(stats)
             e1.record(stream)
             e1.synchronize()
             per_step.append(e0.elapsed_time(e1))
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
+        barrier()
         return per_step, stats
 
-    # the finest-level smoother is timed live by events around the first colour stage
-    # of every smoothing call (2 of its 16 launches per V-cycle): each event removes
-    # the programmatic overlap of the two launches around it
+    def solve_step(g):
+        def step(out):
+            mg.mg_set_field(g, 0, -1, zero)
+            out.append(mg.mg_solve(g, w["branch"], w["alpha"], w["kappa"], TOL))
+        return step
+
+    # FP64: the finest-level smoother is timed live by events around the first colour
+    # stage of every smoothing call (2 of its 16 launches per V-cycle); each event
+    # removes the programmatic overlap of the two launches around it
     g64 = make(mg.MG_FP64, 2)
     with ClockSampler(local) as clk:
-        per_step, stats = timed(g64, args.steps, args.warmup)
+        per_step, stats = timed(solve_step(g64), args.steps, args.warmup)
+        mg.mg_destroy_grid(g64)
+        # mixed precision on the same workload; its finest FP32 colour stages timed alike
+        gmx = make(mg.MG_MIXED, 2)
+        per_step_m, stats_m = timed(solve_step(gmx), args.steps, args.warmup)
+        mg.mg_destroy_grid(gmx)
     clocks = clk.summary()
     total_ms = max_over_ranks(sum(per_step))
-    solves_done = sum_over_ranks(len(solves) * args.steps)
-    value = solves_done / (total_ms * 1e-3)
-
-    # dominant kernel: the finest-level FP64 smoother (one colour stage per launch)
-    k_ms = sum(s["kernel_ms"] for s in stats)
-    k_n = sum(s["kernel_launches"] for s in stats)
-    k_cells = sum(s["kernel_cells"] for s in stats)
-    avg_ms = k_ms / max(k_n, 1)
-    cells_per_launch = k_cells / max(k_n, 1)
-    achieved = FLOP_PER_CELL_FP64 * cells_per_launch / (avg_ms * 1e-3) / 1e12
-    launches = sum(s["launches"] for s in stats)
-    cycles = [s["cycles"] for s in stats[:len(solves)]]
-
-    # mixed precision on the same workload
-    gmx = make(mg.MG_MIXED, 0)
-    per_step_m, stats_m = timed(gmx, args.steps, args.warmup)
     total_m = max_over_ranks(sum(per_step_m))
+    solves_done = sum_over_ranks(args.steps)
+    value = solves_done / (total_ms * 1e-3)
     value_m = solves_done / (total_m * 1e-3)
 
-    # end to end through the C-ABI with pinned host buffers
+    def kernel_rate(st):
+        ms = sum(s["kernel_ms"] for s in st)
+        n = sum(s["kernel_launches"] for s in st)
+        cells = sum(s["kernel_cells"] for s in st)
+        avg_s = ms * 1e-3 / max(n, 1)
+        per = cells / max(n, 1)
+        return avg_s, per, n
+
+    peaks = _peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "MEASURED_PEAKS.json hbm_gbs (STREAM-style copy), of measured"
+    if not hbm_peak:
+        hbm_peak, peak_src = HBM_FALLBACK_GBS, "fallback 6.8 TB/s"
+    # FP32 correction smoother, HBM-bound: algorithmic bytes per launch / event time
+    avg32, cells32, n32 = kernel_rate(stats_m)
+    ach32 = BYTES_PER_CELL_FP32 * cells32 / avg32 / 1e9
+    traffic32 = traffic_per_launch("k_smooth_colour32_n", cells32)
+    # FP64 smoother, bound by the FP64 pipe
+    avg64, cells64, n64 = kernel_rate(stats)
+    ach64 = FLOP_PER_CELL_FP64 * cells64 / avg64 / 1e12
+    traffic64 = traffic_per_launch("k_smooth_colour64", cells64)
+    roofline = {
+        "bound": "hbm", "kernel": f"k_smooth_colour32_n<{N}> (finest FP32 colour stage, mixed)",
+        "achieved": ach32, "peak": hbm_peak, "unit": "GB/s", "frac": ach32 / hbm_peak,
+        "traffic": traffic32, "peak_source": peak_src,
+        "bytes_per_cell": BYTES_PER_CELL_FP32, "cells_per_launch": cells32,
+        "avg_launch_us": avg32 * 1e6, "launches_timed": n32,
+        "traffic_vs_algorithmic": (traffic32 / (BYTES_PER_CELL_FP32 * cells32)
+                                   if traffic32 else None),
+        "fp64": {"bound": "alu", "kernel": f"k_smooth_colour64 (finest FP64 colour stage)",
+                 "achieved": ach64, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                 "frac": ach64 / (FP64_PEAK_GFLOPS / 1e3),
+                 "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                 "flop_per_cell": FLOP_PER_CELL_FP64, "cells_per_launch": cells64,
+                 "avg_launch_us": avg64 * 1e6, "launches_timed": n64, "traffic": traffic64,
+                 "hbm_frac_algorithmic": 24 * cells64 / avg64 / 1e9 / hbm_peak},
+    }
+
+    # the secondary six-solve 128^3 workload (its arrays fit in L2)
+    w2 = workload_secondary()
+    d2 = torch.from_numpy(w2["delta"]).cuda()
+    z2 = torch.zeros_like(d2)
+    sec = {}
+    for name, prec in (("fp64", mg.MG_FP64), ("mixed", mg.MG_MIXED)):
+        g2 = make(prec, 0, N2, d2)
+
+        def step2(out, g2=g2):
+            for s in w2["solves"]:
+                mg.mg_set_field(g2, 0, -1, z2)
+                out.append(mg.mg_solve(g2, s["branch"], s["alpha"], s["kappa"], TOL))
+        ps, st2 = timed(step2, args.steps, args.warmup)
+        mg.mg_destroy_grid(g2)
+        sec[name] = sum_over_ranks(len(w2["solves"]) * args.steps) / (max_over_ranks(sum(ps)) * 1e-3)
+    del d2, z2
+
+    # end to end through the C-ABI with pinned host buffers: density in, initial
+    # guess in, solve, field out, every step
     host_delta = torch.from_numpy(delta_np).pin_memory()
     host_zero = torch.zeros(delta_np.shape, dtype=torch.float64).pin_memory()
     host_out = torch.empty(delta_np.shape, dtype=torch.float64).pin_memory()
@@ -273,14 +354,13 @@ def run_ours(args):
 
     def e2e_step():
         mg.mg_set_density(ge, 0, -1, host_delta)
-        for s in solves:
-            mg.mg_set_field(ge, 0, -1, host_zero)
-            mg.mg_solve(ge, s["branch"], s["alpha"], s["kappa"], TOL)
-            mg.mg_get_field(ge, 0, -1, host_out)
+        mg.mg_set_field(ge, 0, -1, host_zero)
+        mg.mg_solve(ge, w["branch"], w["alpha"], w["kappa"], TOL)
+        mg.mg_get_field(ge, 0, -1, host_out)
 
     for _ in range(args.warmup):
         e2e_step()
-    torch.cuda.synchronize()
+    barrier()
     e2e_ms = []
     for _ in range(args.steps):
         flush.zero_()
@@ -289,49 +369,46 @@ def run_ours(args):
         e2e_step()
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    barrier()
+    mg.mg_destroy_grid(ge)
     e2e_total = max_over_ranks(sum(e2e_ms))
     cell_bytes = delta_np.size * 8
     e2e = {"value": solves_done / (e2e_total * 1e-3), "unit": "solves/s",
-           "h2d_bytes_per_step": cell_bytes * (1 + len(solves)),
-           "d2h_bytes_per_step": cell_bytes * len(solves)}
-    for h in (g64, gmx, ge):
-        mg.mg_destroy_grid(h)
+           "h2d_bytes_per_step": 2 * cell_bytes, "d2h_bytes_per_step": cell_bytes}
 
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        peaks = json.load(open(pk))
+    s0, m0 = stats[0], stats_m[0]
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "128^3 periodic lognormal delta (sigma 1.5, P(k)~k^-2, seed 1302), "
-                               "6 solves: r_V = 2, 8, 32 cells x both signs of alpha, FP64, "
-                               "max|d - lambda| < 1e-8 from phi = 0",
-                   "n": N, "solves_per_step": len(solves), "tol": TOL, "precision": "fp64",
+        "config": {"workload": WORKLOAD, "n": N, "sigma": SIGMA, "seed": SEED,
+                   "alpha_kappa": w["alpha"], "solves_per_step": 1, "tol": TOL,
+                   "precision": "fp64 (value); mixed under 'mixed'",
                    "nu_pre": 2, "nu_post": 2, "coarsest": 4,
-                   "l2": "flushed before every timed step (256 MiB write)",
-                   "cycles_per_solve": cycles},
-        "roofline": {"bound": "alu", "kernel": "k_smooth_colour64 (finest level)",
-                     "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                     "frac": achieved / (FP64_PEAK_GFLOPS / 1e3),
-                     "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-                     "flop_per_cell": FLOP_PER_CELL_FP64, "cells_per_launch": cells_per_launch,
-                     "avg_launch_us": avg_ms * 1e3, "launches_timed": k_n,
-                     "traffic": traffic_per_launch("k_smooth_colour64")},
-        "smoother": {"fp64_cell_updates_per_s": cells_per_launch / (avg_ms * 1e-3)},
+                   "l2": "flushed before every timed step (256 MiB write); every 512^3 "
+                         "array (1.07 GB FP64, 0.54 GB FP32) is larger than L2",
+                   "cycles_per_solve": s0["cycles"], "res": s0["res"],
+                   "floored_cells": s0["guard_hits"],
+                   "floored_fraction": s0["guard_hits"] / float(N ** 3)},
+        "roofline": roofline,
+        "smoother": {"fp64_cell_updates_per_s": cells64 / avg64,
+                     "fp32_cell_updates_per_s": cells32 / avg32},
         "mixed": {"value": value_m, "unit": "solves/s", "ms_per_step": total_m / args.steps,
-                  "speedup_vs_fp64": value_m / value,
-                  "outer_per_solve": [s["outer"] for s in stats_m[:len(solves)]],
-                  "inner_cycles_per_solve": [s["cycles"] for s in stats_m[:len(solves)]]},
+                  "speedup_vs_fp64": value_m / value, "outer_per_solve": m0["outer"],
+                  "inner_cycles_per_solve": m0["cycles"], "res": m0["res"],
+                  "floored_cells": m0["guard_hits"]},
+        "secondary": {"workload": "128^3 lognormal (sigma 1.5, seed 1302), six solves "
+                                  "(r_V = 2, 8, 32 cells x both signs) per step to 1e-8",
+                      "fp64_solves_per_s": sec["fp64"], "mixed_solves_per_s": sec["mixed"]},
         "e2e": e2e,
-        "gpu_launches": launches,
+        "gpu_launches": sum(s["launches"] for s in stats),
+        "gpu_launches_mixed": sum(s["launches"] for s in stats_m),
         "clocks": clocks,
-        "hbm_peak_gbs": peaks.get("hbm_gbs"),
+        "hbm_peak_gbs": hbm_peak,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, 1)
+        line["cpu_baseline"] = cpu_baseline(w, s0["cycles"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -339,49 +416,112 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
-# the CPU oracle
+# the CPU oracle (four-colour OpenMP build on all host cores)
 # ---------------------------------------------------------------------------
-def cpu_baseline(w, count):
-    """The oracle as it stands, single thread, on `count` of the six solves."""
+SAMPLE_CYCLES = 2
+
+
+def host_cores():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("CPU(s):"):
+                return int(line.split(":")[1])
+    except OSError:
+        pass
+    return os.cpu_count()
+
+
+def oracle_sample(w, delta_floor):
+    """One bounded sample of an oracle solve of the workload: the set-up alone
+    (allocation, restriction of delta, first residual) and then the set-up plus
+    SAMPLE_CYCLES V-cycles from phi = 0, on all host cores.  The solve time is
+    estimated as set-up + cycles needed x time per cycle, the cycles needed being
+    extrapolated from the sampled residual reduction."""
     from oracle import oracle as O
     t0 = time.perf_counter()
-    for i in range(count):
-        s = w["solves"][(2 + i) % len(w["solves"])]
-        delta, _ = O.density_floor(w["delta"], s["alpha"], s["kappa"])
-        O.fas_solve(delta, s["alpha"], s["kappa"], s["branch"], tol=TOL)
-    dt = time.perf_counter() - t0
-    return {"value": count / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{count} of the 6 solves of the 128^3 workload (r_V = 8 cells first), "
-                      f"single-threaded lexicographic FAS, {dt:.1f} s"}
+    _, s0 = O.fas_solve_colour(delta_floor, w["alpha"], w["kappa"], w["branch"], tol=TOL,
+                               max_cycles=0)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, st = O.fas_solve_colour(delta_floor, w["alpha"], w["kappa"], w["branch"], tol=TOL,
+                               max_cycles=SAMPLE_CYCLES)
+    t_run = time.perf_counter() - t0
+    t_cycle = max(t_run - t_setup, 1e-9) / max(st["cycles"], 1)
+    res0, resk = st["res0"], st["res"]
+    if st["cycles"] and resk < res0:
+        rate = (resk / res0) ** (1.0 / st["cycles"])
+        need = max(st["cycles"], math.ceil(math.log(TOL / res0) / math.log(rate)))
+    else:
+        need = None
+    est = t_setup + need * t_cycle if need else None
+    return {"t_setup": t_setup, "t_cycle": t_cycle, "cycles_needed": need, "solve_s": est,
+            "threads": st["threads"], "res0": res0, "res_sampled": resk,
+            "sample_s": t_setup + t_run}
+
+
+def cpu_baseline(w, gpu_cycles):
+    import numpy as np
+    from oracle import oracle as O
+    fl, _ = O.density_floor(w["delta"], w["alpha"], w["kappa"])
+    smp = oracle_sample(w, fl)
+    t0 = time.perf_counter()
+    _, threads = O.colour_sweeps(np.zeros_like(fl), fl, w["alpha"], w["kappa"], w["branch"],
+                                 sweeps=1)
+    sweep_rate = fl.size / (time.perf_counter() - t0)
+    return {"value": 1.0 / smp["solve_s"] if smp["solve_s"] else None, "unit": "solves/s",
+            "cores": smp["threads"], "host_cpus_lscpu": host_cores(),
+            "kind": "oracle (four-colour Newton-Gauss-Seidel FAS, OpenMP on all host cores)",
+            "sample": (f"set-up plus {SAMPLE_CYCLES} V-cycles of the {N}^3 solve from phi = 0 "
+                       f"({smp['sample_s']:.1f} s); solve time = set-up {smp['t_setup']:.2f} s + "
+                       f"{smp['cycles_needed']} cycles x {smp['t_cycle']:.2f} s, the cycle count "
+                       f"extrapolated from the sampled residual drop "
+                       f"{smp['res0']:.3g} -> {smp['res_sampled']:.3g} (the GPU FP64 solve took "
+                       f"{gpu_cycles} cycles)"),
+            "sweep_cell_updates_per_s": sweep_rate, "sweep_threads": threads}
 
 
 def run_reference(args):
+    """The oracle on the host cores of rank 0.  The first warm-up step takes the full
+    sample of oracle_sample (set-up time and the extrapolated cycle count); the other
+    warm-up steps repeat the set-up only.  Each timed step runs the set-up and one
+    V-cycle from phi = 0, and is scaled to one solve by the cycles still needed at
+    the time per cycle it measured."""
     rank, ws, _ = world()
     if rank != 0:
         return
-    w = workload()
     from oracle import oracle as O
-    times = []
-    k = 0
-    for it in range(args.warmup + args.steps):
-        s = w["solves"][k % len(w["solves"])]
-        k += 1
+    w = workload()
+    fl, hits = O.density_floor(w["delta"], w["alpha"], w["kappa"])
+    first = oracle_sample(w, fl)
+    need, t_setup = first["cycles_needed"], first["t_setup"]
+    for _ in range(args.warmup - 1):
+        O.fas_solve_colour(fl, w["alpha"], w["kappa"], w["branch"], tol=TOL, max_cycles=0)
+    est = []
+    threads = first["threads"]
+    for _ in range(args.steps):
         t0 = time.perf_counter()
-        # the system the GPU solves: source held at the real-root bound (default guard)
-        delta, _ = O.density_floor(w["delta"], s["alpha"], s["kappa"])
-        O.fas_solve(delta, s["alpha"], s["kappa"], s["branch"], tol=TOL)
-        if it >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    total = sum(times)
-    value = len(times) / total
+        _, st = O.fas_solve_colour(fl, w["alpha"], w["kappa"], w["branch"], tol=TOL,
+                                   max_cycles=1)
+        t_step = time.perf_counter() - t0
+        threads = st["threads"]
+        est.append(t_step + (need - 1) * max(t_step - t_setup, 0.0))
+    total = sum(est)
+    value = len(est) / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "ms_per_step": 1e3 * total / len(est), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "128^3 periodic lognormal delta (sigma 1.5, P(k)~k^-2, "
-                                   "seed 1302), 6 solves to 1e-8; one solve per step"},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": "one of the six 128^3 solves per step, cycling"},
+            "config": {"workload": WORKLOAD, "n": N, "sigma": SIGMA, "seed": SEED,
+                       "alpha_kappa": w["alpha"], "tol": TOL, "floored_cells": hits},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads,
+                             "host_cpus_lscpu": host_cores(),
+                             "kind": "oracle (four-colour Newton-Gauss-Seidel FAS, OpenMP)",
+                             "sample": (f"per step: set-up plus one V-cycle of the {N}^3 solve "
+                                        f"from phi = 0, scaled to one solve by the {need} "
+                                        f"cycles extrapolated from the residual drop of "
+                                        f"{SAMPLE_CYCLES} cycles in the first warm-up step "
+                                        f"({first['res0']:.3g} -> {first['res_sampled']:.3g})")},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -1,9 +1,9 @@
 """One solve of a lognormal workload through the C-ABI, for profiling a kernel.
 
-  python -m paper_1303_0008_gb300.profile_case --n 256 --prec fp64 --rv 8
-  python -m paper_1303_0008_gb300.profile_case --six --prec fp64
+  python benchmarks/profile_case.py --n 256 --prec fp64 --rv 8
+  python benchmarks/profile_case.py --six --prec fp64
 
-Runs a single periodic solve (sigma 1.5, seed 1302) to 1e-8 on cuda:0, or with
+Runs a single periodic solve (default sigma 1.5, seed 1302) to 1e-8 on cuda:0, or with
 --six the six solves of one step of the benchmark, and prints the statistics of
 each solve as one JSON line.  --case selects the other kernel families: a
 refined hierarchy, the batched solves, or particle assignment with refinement.  Meant to be run under a profiler with a kernel
@@ -29,12 +29,18 @@ def main(argv=None):
     p.add_argument("--prec", choices=["fp64", "mixed"], default="fp64")
     p.add_argument("--rv", type=float, default=8.0)
     p.add_argument("--sigma", type=float, default=1.5)
+    p.add_argument("--seed", type=int, default=1302)
     p.add_argument("--tol", type=float, default=1e-8)
     p.add_argument("--six", action="store_true",
                    help="run the six solves of one benchmark step (128^3 lognormal, "
                         "r_V = 2, 8, 32 cells, both signs) instead of a single solve")
     p.add_argument("--sweep32", type=int, default=0)
-    p.add_argument("--case", choices=["solve", "refined", "batch", "particles"], default="solve",
+    p.add_argument("--galerkin", type=int, default=1,
+                   help="coarse-grid correction of the refinement unions (c3 case)")
+    p.add_argument("--alpha", type=float, default=None,
+                   help="alpha*kappa of the c3 case (default r_V = 8 cells, 0.3)")
+    p.add_argument("--case", choices=["solve", "refined", "batch", "particles", "c3"],
+                   default="solve",
                    help="refined: a 128^3 sigma 2.0 domain with two refinement levels "
                         "(alpha*kappa 1e-3); batch: the 64-solve mixed batch; particles: "
                         "TSC assignment of 2^24 particles and the N_pc = 9 criterion at 256^3")
@@ -53,7 +59,7 @@ def main(argv=None):
         solves = w["solves"]
         n = 128
     else:
-        delta = torch.from_numpy(inputs.lognormal_delta(args.n, args.sigma, 1302)).cuda()
+        delta = torch.from_numpy(inputs.lognormal_delta(args.n, args.sigma, args.seed)).cuda()
         solves = [{"alpha": inputs.alpha_kappa_for_rv(args.rv), "kappa": 1.0, "branch": 0}]
         n = args.n
     g = mg.mg_create_grid(n, mg.options(prec=prec, sweep32=args.sweep32))
@@ -74,8 +80,42 @@ def main(argv=None):
 
 
 def other_case(args, torch, inputs, mg):
+    import time
+
     import numpy as np
-    if args.case == "refined":
+    if args.case == "c3":
+        # the 256^3 domain with two refinement levels (sigma 2, seed 1303)
+        h = inputs.refined_hierarchy(256, 2.0, 1303)
+        alpha = args.alpha if args.alpha is not None else inputs.alpha_kappa_for_rv(8.0)
+        g = mg.mg_create_grid(256, mg.options(patch_galerkin=args.galerkin))
+        try:
+            mg.mg_set_density(g, 0, -1, h["delta0"])
+            for lvl, L in enumerate(h["levels"], start=1):
+                mg.mg_add_patches(g, lvl, L["origins"])
+                mg.mg_set_density(g, lvl, -1, np.ascontiguousarray(L["delta"]))
+            out = []
+            for rep in range(2):
+                zero = np.zeros_like(h["delta0"])
+                mg.mg_set_field(g, 0, -1, zero)
+                for lvl, L in enumerate(h["levels"], start=1):
+                    mg.mg_set_field(g, lvl, -1, np.zeros((len(L["origins"]), 8, 8, 8)))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = mg.mg_solve(g, 0, alpha, 1.0, args.tol, check=False)
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - t0
+                lv = [mg.mg_get_level_stats(g, lvl) for lvl in (1, 2)]
+                out.append({"rep": rep, "rc": st["rc"], "wall_s": wall,
+                            "domain": {"cycles": st["cycles"], "wall_s": st["wall_s"]},
+                            "levels": [{"cycles": s["cycles"], "status": s["status"],
+                                        "res": s["res"], "wall_s": s["wall_s"],
+                                        "hist": s["hist"][:60]} for s in lv]})
+        finally:
+            mg.mg_destroy_grid(g)
+        for o in out:
+            print(json.dumps({"case": "c3", "galerkin": args.galerkin, "alpha": alpha,
+                              "patches": [len(L["origins"]) for L in h["levels"]], **o}))
+    elif args.case == "refined":
         h = inputs.refined_hierarchy(128, 2.0, 1303)
         g = mg.mg_create_grid(128)
         try:

@@ -1,6 +1,6 @@
 """Measure the five workload configurations through the C-ABI on cuda:0.
 
-  python -m paper_1303_0008_gb300.run_configs [--only C1,C4] [--reps 3]
+  python benchmarks/run_configs.py [--only C1,C4] [--reps 3]
 
 C1  32^3 top-hat (delta 10 in radius 4 cells), r_V = 8 cells, FP64
 C2  128^3 lognormal (sigma 1.5), r_V = 2, 8, 32 cells x both signs, FP64

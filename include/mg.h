@@ -132,6 +132,13 @@ typedef struct {
                         the cell's own value and each smoothing update a full Newton step
                         with the Jacobian diagonal of Sec. III.B; FP64 domain solves only
                         (MG_EINVAL with MG_MIXED, refinement levels or batches). */
+  int patch_galerkin;/* coarse-grid correction of refinement unions: 1 (default) solves
+                        the linear correction equation with Galerkin coarse operators
+                        R J P of the union's Jacobian J at the current iterate (FP32,
+                        eight-colour Gauss-Seidel on the 27-point coarse operators);
+                        0 uses the FAS coarse equations with the rediscretised operator.
+                        The converged solution is the same; with alpha*kappa*delta >> 1
+                        in dense regions only the Galerkin correction converges. */
 } mg_options;
 
 typedef struct {
@@ -247,7 +254,8 @@ mg_status mg_autotune(mg_grid* g, int branch, double alpha, double kappa, double
                       double* best_seconds);
 
 /* Statistics of the last solve of a refinement level (level >= 1): cycles,
- * status, final residual and the residual after each cycle. */
+ * status, final residual, the residual after each cycle and the device time of
+ * its V-cycles (wall_s). */
 mg_status mg_get_level_stats(const mg_grid* g, int level, mg_solve_stats* out);
 
 /* Release the handle and all of its device memory.  NULL is ignored. */
@@ -343,7 +351,7 @@ mg_status mg_solve_batch(mg_grid* g, const int* branch, const double* alpha, con
  * d = L^h phi - f (Sec. III.C residual; L^h of Sec. III.B), h = 1/n.  f may be
  * NULL (f = 0); d may be NULL (norms only).  norms (host, 5 doubles, may be
  * NULL): [sum d, max d, min d, guarded cells, non-finite cells].  Synchronises
- * the stream when norms is given.
+ * the stream before it returns.
  */
 mg_status mg_op_residual(int n, const double* phi, const double* delta, const double* f,
                          int branch, double alpha, double kappa, double* d, double* norms,
@@ -379,7 +387,11 @@ mg_status mg_op_force(int n, const double* phi, double* out, void* stream);
  *     GPU race on it, so the caller must order them (one stream, or events).
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
- * Errors: MG_EINVAL (size, branch, NULL input), MG_ECUDA.
+ *     The address is kept for the life of the process: do not call this entry
+ *     point again after cudaDeviceReset.
+ *   - Like mg_op_residual, the call synchronises `stream` before it returns,
+ *     whether or not norms is given, and reports execution errors.
+ * Errors: MG_EINVAL (size, branch, non-finite alpha, NULL input), MG_ECUDA.
  */
 mg_status mg_op_residual_noalloc(int n, const double* phi, const double* delta, const double* f,
                                  int branch, double alpha, double kappa, double* d, double* norms,

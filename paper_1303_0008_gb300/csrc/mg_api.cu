@@ -51,6 +51,7 @@ void mg_default_options(mg_options* opt) {
   opt->pair32 = 0;
   opt->tau_stop = 0.0;
   opt->w = 1.0 / 3.0;
+  opt->patch_galerkin = 1;
 }
 
 static mg_status check_options(const mg_options& o) {
@@ -76,6 +77,7 @@ static mg_status check_options(const mg_options& o) {
   if (o.pair32 != 0 && o.pair32 != 1) MG_FAIL(MG_EINVAL, "options: pair32");
   if (!(o.tau_stop >= 0.0 && o.tau_stop < 1e3)) MG_FAIL(MG_EINVAL, "options: tau_stop");
   if (!(o.w >= 0.0 && o.w < 1.0)) MG_FAIL(MG_EINVAL, "options: w");
+  if (o.patch_galerkin != 0 && o.patch_galerkin != 1) MG_FAIL(MG_EINVAL, "options: patch_galerkin");
   return MG_OK;
 }
 
@@ -168,6 +170,7 @@ mg_status mg_get_level_stats(const mg_grid* g, int level, mg_solve_stats* out) {
   out->status = pl->last_status;
   out->levels = 3;
   out->res = pl->last_res;
+  out->wall_s = pl->last_wall_s;
   out->res0 = pl->last_hist.empty() ? 0.0 : pl->last_hist.front();
   for (double r : pl->last_hist)
     if (out->hist_len < 128) out->res_hist[out->hist_len++] = r;

@@ -17,6 +17,8 @@
 // every entry it reads, so nothing has to be cleared between calls.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <cmath>
 #include <string>
 
 #include "../../include/mg.h"
@@ -64,9 +66,12 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_residual64_noalloc(
   if (threadIdx.x == 0) scratch->partials[blockIdx.x] = p;
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device.  Host threads
+// may race to fill an entry; they all store the same address.  The address
+// belongs to the device's primary context: after cudaDeviceReset it is stale,
+// and this entry point must not be used again in that process.
 static constexpr int kMaxDevices = 64;
-static NoAllocScratch* g_scratch_ptr[kMaxDevices] = {};
+static std::atomic<NoAllocScratch*> g_scratch_ptr[kMaxDevices] = {};
 
 static mg_status scratch_for_current_device(NoAllocScratch** out) {
   int dev = 0;
@@ -79,7 +84,8 @@ static mg_status scratch_for_current_device(NoAllocScratch** out) {
     set_error("mg_op_residual_noalloc: device index out of range");
     return MG_EINVAL;
   }
-  if (!g_scratch_ptr[dev]) {
+  NoAllocScratch* cached = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!cached) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || !ptr) {
@@ -87,9 +93,10 @@ static mg_status scratch_for_current_device(NoAllocScratch** out) {
                 cudaGetErrorString(e));
       return MG_ECUDA;
     }
-    g_scratch_ptr[dev] = (NoAllocScratch*)ptr;
+    cached = (NoAllocScratch*)ptr;
+    g_scratch_ptr[dev].store(cached, std::memory_order_release);
   }
-  *out = g_scratch_ptr[dev];
+  *out = cached;
   return MG_OK;
 }
 
@@ -110,8 +117,9 @@ extern "C" mg_status mg_op_residual_noalloc(int n, const double* phi, const doub
               " exceeds the maximum of 256 (its fixed scratch covers 256^3 cells)");
     return MG_EINVAL;
   }
-  if (branch < -1 || branch > 1 || (alpha == 0.0 && branch != 0) || !phi || !delta) {
-    set_error("mg_op_residual_noalloc: bad branch, alpha or NULL input");
+  if (branch < -1 || branch > 1 || (alpha == 0.0 && branch != 0) || !std::isfinite(alpha) ||
+      !phi || !delta) {
+    set_error("mg_op_residual_noalloc: bad branch, non-finite alpha or NULL input");
     return MG_EINVAL;
   }
   NoAllocScratch* scratch = nullptr;
@@ -131,14 +139,16 @@ extern "C" mg_status mg_op_residual_noalloc(int n, const double* phi, const doub
     set_error(std::string("mg_op_residual_noalloc: launch: ") + cudaGetErrorString(e));
     return MG_ECUDA;
   }
+  // like mg_op_residual, the call returns once the kernels have finished, so that
+  // an execution error is reported here whether or not the norms are wanted
+  LevelScalars h;
+  e = cudaMemcpyAsync(&h, &scratch->scalars, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_error(std::string("mg_op_residual_noalloc: ") + cudaGetErrorString(e));
+    return MG_ECUDA;
+  }
   if (norms) {
-    LevelScalars h;
-    e = cudaMemcpyAsync(&h, &scratch->scalars, sizeof(h), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      set_error(std::string("mg_op_residual_noalloc: ") + cudaGetErrorString(e));
-      return MG_ECUDA;
-    }
     norms[0] = h.sum;
     norms[1] = h.dmax;
     norms[2] = h.dmin;

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "mg_internal.h"
+#include "mg_patch_tile.cuh"
 #include "mg_solver.h"
 
 namespace mg {
@@ -63,52 +64,6 @@ __device__ __forceinline__ double fetch(const FieldSrc& s, int x, int y, int z) 
     return 0.0;
   }
   return s.pphi[(long long)q * 512 + (x & 7) + 8 * ((y & 7) + 8 * (z & 7))];
-}
-
-// Load the ghosted tile of patch p at block size B into shared memory.
-template <int B>
-__device__ __forceinline__ void load_tile(double* __restrict__ tile, int p,
-                                          const double* __restrict__ phi,
-                                          const double* __restrict__ ghost,
-                                          const int* __restrict__ nbr) {
-  constexpr int T = B + 2, TC = T * T * T, BC = B * B * B;
-  for (int q = threadIdx.x; q < TC; q += blockDim.x) {
-    const int i = q % T - 1, j = (q / T) % T - 1, k = q / (T * T) - 1;
-    const int ox = i < 0 ? -1 : (i >= B ? 1 : 0);
-    const int oy = j < 0 ? -1 : (j >= B ? 1 : 0);
-    const int oz = k < 0 ? -1 : (k >= B ? 1 : 0);
-    double v;
-    if ((ox | oy | oz) == 0) {
-      v = phi[(long long)p * BC + i + B * (j + B * k)];
-    } else {
-      const int nb = nbr[p * 27 + (ox + 1) + 3 * ((oy + 1) + 3 * (oz + 1))];
-      if (nb >= 0)
-        v = phi[(long long)nb * BC + (i - ox * B) + B * ((j - oy * B) + B * (k - oz * B))];
-      else
-        v = ghost[(long long)p * TC + q];
-    }
-    tile[q] = v;
-  }
-}
-
-template <int B>
-__device__ __forceinline__ StencilT<double> gather_tile(const double* tile, int i, int j, int k) {
-  constexpr int T = B + 2;
-  auto at = [&](int a, int b, int c) { return tile[(a + 1) + T * ((b + 1) + T * (c + 1))]; };
-  StencilT<double> s;
-  s.sx = at(i + 1, j, k) + at(i - 1, j, k);
-  s.sy = at(i, j + 1, k) + at(i, j - 1, k);
-  s.sz = at(i, j, k + 1) + at(i, j, k - 1);
-  s.cxy = (at(i + 1, j + 1, k) + at(i - 1, j - 1, k)) - (at(i + 1, j - 1, k) + at(i - 1, j + 1, k));
-  s.cxz = (at(i + 1, j, k + 1) + at(i - 1, j, k - 1)) - (at(i + 1, j, k - 1) + at(i - 1, j, k + 1));
-  s.cyz = (at(i, j + 1, k + 1) + at(i, j - 1, k - 1)) - (at(i, j + 1, k - 1) + at(i, j - 1, k + 1));
-  return s;
-}
-
-template <int B>
-__device__ __forceinline__ double tile_ctr(const double* tile, int i, int j, int k) {
-  constexpr int T = B + 2;
-  return tile[(i + 1) + T * ((j + 1) + T * (k + 1))];
 }
 
 // ---------------------------------------------------------------------------
@@ -363,6 +318,7 @@ void patch_level_destroy(PatchLevel* pl) {
   cudaFree(pl->d_part);
   cudaFree(pl->d_err);
   cudaFree(pl->d_coarse_parent);
+  galerkin_release(pl);
   delete pl;
 }
 
@@ -569,7 +525,10 @@ struct PatchCycle {
   }
 
   void part_b() const {
-    if (mlev() > 1) {
+    if (mlev() > 1 && o->patch_galerkin) {
+      // linear correction with Galerkin coarse operators; f_c[1] holds R d
+      galerkin_correction(st, pl, *o, ops[0], pl->f_c[1], mlev());
+    } else if (mlev() > 1) {
       fas_rhs(1);
       descend(1);
       prolong(0);
@@ -637,6 +596,14 @@ mg_status patch_level_solve(mg_grid* g, int level, int branch, double alpha, dou
               ": a Dirichlet value needs a parent cell that is not refined (proper nesting)");
     return MG_EINVAL;
   }
+  if (g->opt.patch_galerkin && g->opt.patch_mg_levels > 1) {
+    mg_status gs = galerkin_prepare(pl);
+    if (gs != MG_OK) return gs;
+  }
+  cudaEvent_t w0 = nullptr, w1 = nullptr;
+  PCK(cudaEventCreate(&w0));
+  PCK(cudaEventCreate(&w1));
+  PCK(cudaEventRecord(w0, st));
   // V-cycles on the union
   long long na = 0, nb = 0;
   cudaGraphExec_t ga = nullptr, gb = nullptr;
@@ -679,6 +646,13 @@ mg_status patch_level_solve(mg_grid* g, int level, int branch, double alpha, dou
       cyc.part_b();
     }
   }
+  if (cudaEventRecord(w1, st) == cudaSuccess && cudaEventSynchronize(w1) == cudaSuccess) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, w0, w1);
+    pl->last_wall_s = ms * 1e-3;
+  }
+  cudaEventDestroy(w0);
+  cudaEventDestroy(w1);
   pl->last_cycles = (int)hist.size() - 1;
   pl->last_res = hist.empty() ? 0.0 : hist.back();
   pl->last_status = result;

@@ -75,7 +75,13 @@ struct PatchLevel {
   int* d_table = nullptr;           // (nside/8)^3 block -> patch index or -1
   int* d_err = nullptr;             // set when a Dirichlet value finds no parent cell
   double* d_coarse_parent = nullptr;  // level 1: the domain field restricted once
+  // linear (Galerkin) coarse-grid correction of the union, union levels 1 and 2:
+  // 27-point operator [count][27][cells per patch], correction and right-hand side
+  float* gJ[3] = {nullptr, nullptr, nullptr};
+  float* ge[3] = {nullptr, nullptr, nullptr};
+  float* gb[3] = {nullptr, nullptr, nullptr};
   int last_cycles = 0;
+  double last_wall_s = 0.0;  // device time of the last solve of this level (V-cycles)
   double last_res = 0.0;
   int last_status = 0;
   std::vector<double> last_hist;
@@ -121,6 +127,12 @@ mg_status patch_level_solve(mg_grid* g, int level, int branch, double alpha, dou
                             double tol);
 mg_status patch_force(mg_grid* g, int level, int patch, double* out);
 void patch_restrict_density(mg_grid* g, PatchLevel* pl);
+
+// mg_patch_galerkin.cu
+mg_status galerkin_prepare(PatchLevel* pl);
+void galerkin_release(PatchLevel* pl);
+void galerkin_correction(cudaStream_t st, PatchLevel* pl, const mg_options& o,
+                         const OpConst64& op0, const double* rd, int mlev);
 
 // mg_batch.cu
 mg_status batch_prepare(mg_grid* g);

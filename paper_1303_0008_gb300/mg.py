@@ -39,7 +39,8 @@ class mg_options(ctypes.Structure):
                 ("omega", ctypes.c_double), ("omega_patch", ctypes.c_double),
                 ("patch_mg_levels", ctypes.c_int), ("patch_cgc", ctypes.c_double),
                 ("sweep32", ctypes.c_int), ("pair32", ctypes.c_int),
-                ("tau_stop", ctypes.c_double), ("w", ctypes.c_double)]
+                ("tau_stop", ctypes.c_double), ("w", ctypes.c_double),
+                ("patch_galerkin", ctypes.c_int)]
 
 
 class mg_solve_stats(ctypes.Structure):
@@ -359,11 +360,15 @@ def mg_op_prolong_correct(n, coarse, coarse_ref, fine, stream=None):
                                        _stream(stream)), "mg_op_prolong_correct")
 
 
-def mg_op_residual_noalloc(n, phi, delta, f, branch, alpha, kappa, d=None, stream=None):
-    """mg_op_residual for callers that cannot allocate device memory (n <= 256)."""
-    norms = (ctypes.c_double * 5)()
+def mg_op_residual_noalloc(n, phi, delta, f, branch, alpha, kappa, d=None, stream=None,
+                           want_norms=True):
+    """mg_op_residual for callers that cannot allocate device memory (n <= 256).
+    With want_norms=False the C call gets a NULL norms pointer and None is returned."""
+    norms = (ctypes.c_double * 5)() if want_norms else None
     _check(lib().mg_op_residual_noalloc(n, _dev(phi), _dev(delta), _dev(f), branch, alpha, kappa,
                                         _dev(d), norms, _stream(stream)), "mg_op_residual_noalloc")
+    if norms is None:
+        return None
     return {"sum": norms[0], "max": norms[1], "min": norms[2], "guards": int(norms[3]),
             "nonfinite": int(norms[4])}
 

@@ -46,20 +46,34 @@ def test_single_process_aggregation_is_identity():
     assert bench.max_over_ranks(3.5) == 3.5 and bench.sum_over_ranks(6.0) == 6.0
 
 
-def test_traffic_record_matches_the_smoother_source():
-    """The benchmark's DRAM-traffic figure is tied to a hash of the finest-level
-    smoother's source (both headers of its body, the kernel, its launcher and the
-    block-size rule).  The three definitions must still be found, and the committed
-    record must carry the current hash, else the benchmark reports no traffic."""
+@pytest.mark.parametrize("kernel", ["k_smooth_colour64", "k_smooth_colour32_n"])
+def test_traffic_record_matches_the_smoother_source(kernel):
+    """The benchmark's DRAM-traffic figures are tied to a hash of each roofline
+    kernel's source (the headers of its body, the kernel and its launcher).  The
+    definitions must still be found, and the committed record must carry the current
+    hash, else the benchmark reports no traffic for that kernel."""
     import json
     import bench
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    csrc = os.path.join(root, "paper_1303_0008_gb300", "csrc", "mg_fp64.cu")
-    text = open(csrc).read()
-    for head in ("__global__ void __launch_bounds__(256) k_smooth_colour64(",
-                 "int tpb_for(long long items)", "void launch_smooth64("):
+    headers, unit, heads = bench._KERNEL_SOURCES[kernel]
+    text = open(os.path.join(root, "paper_1303_0008_gb300", "csrc", unit)).read()
+    for head in heads:
         part = bench._definition(text, head)
         assert part.startswith(head) and part.rstrip().endswith("}")
-    rec = json.load(open(os.path.join(root, "profiles", "traffic.json")))["k_smooth_colour64"]
-    assert rec["source_hash"] == bench.kernel_source_hash()
-    assert bench.traffic_per_launch("k_smooth_colour64") == rec["bytes_per_launch_full_size"] > 0
+    rec = json.load(open(os.path.join(root, "profiles", "traffic.json")))[kernel]
+    assert rec["source_hash"] == bench.kernel_source_hash(kernel)
+    full = bench.traffic_per_launch(kernel, 2 * rec["cells_per_launch"])
+    assert full == 2 * rec["bytes_per_launch"] > 0
+
+
+def test_reference_arm_prints_one_line(capsys, monkeypatch):
+    """The reference arm on a small grid: one JSON line with the contract's keys."""
+    import json
+    import bench
+    monkeypatch.setattr(bench, "N", 32)
+    monkeypatch.setattr(bench, "SAMPLE_CYCLES", 2)
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "solves/s" and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0

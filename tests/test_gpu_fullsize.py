@@ -22,17 +22,16 @@ def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("sigma,alpha,min_patches", [(2.0, 1e-3, (60000, 4000)),
+@pytest.mark.parametrize("sigma,alpha,min_patches", [(2.0, 0.3, (60000, 4000)),
                                                      (1.0, 0.3, (3000,))])
 def test_c3_refined_levels_full_size(sigma, alpha, min_patches):
-    """256^3 domain with two refinement criteria (delta > 20, then > 80).
+    """256^3 domain with two refinement criteria (delta > 20, then > 80), r_V = 8
+    cells (alpha*kappa = 0.3).
 
     sigma 2.0 gives 72,167 level-1 and 4,449 level-2 patches; the level-1 density
-    reaches delta = 3382 with 10% noise at the cell scale, and from alpha*kappa ~ 3e-3
-    up, alpha*kappa*delta ~ 16 there makes the linearised operator strongly
-    anisotropic cell by cell and the union FAS correction diverges, so this case
-    runs at alpha*kappa = 1e-3.  sigma 1.0 gives 3,124 level-1 patches (no level 2)
-    and runs at r_V = 8 cells (alpha*kappa = 0.3)."""
+    reaches delta = 3382 with 10% noise at the cell scale, alpha*kappa*delta ~ 1000.
+    The unions converge with the Galerkin coarse-grid correction (the default).
+    sigma 1.0 gives 3,124 level-1 patches (no level 2)."""
     h = I.refined_hierarchy(256, sigma, 1303)
     levels = h["levels"]
     counts = [len(L["origins"]) for L in levels if len(L["origins"])]

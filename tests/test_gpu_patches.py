@@ -61,9 +61,12 @@ def small():
     return I.refined_hierarchy(16, 2.0, 5, thresholds=(15.0, 40.0))
 
 
-def test_refined_levels_match_oracle(small):
+@pytest.mark.parametrize("galerkin", [1, 0])
+def test_refined_levels_match_oracle(small, galerkin):
+    """Both coarse-grid corrections of the union (Galerkin, the default, and the
+    rediscretised FAS) reach the oracle's solution of each level."""
     h = small
-    res = solve_hierarchy(h)
+    res = solve_hierarchy(h, patch_galerkin=galerkin)
     assert res["stats"]["rc"] == mg.MG_OK, res["stats"]
     l1, l2 = h["levels"]
     # level 1 against the oracle, Dirichlet values from the GPU's domain solution
@@ -152,3 +155,54 @@ def test_patch_errors():
         assert st["rc"] == mg.MG_EINVAL and "nesting" in mg.mg_last_error()
     finally:
         mg.mg_destroy_grid(g)
+
+
+def _levels_vs_oracle(h, res, alpha, tol_rel):
+    n0 = h["delta0"].shape[0]
+    l1, l2 = h["levels"]
+    ref1, st1 = O.patch_solve(n0, 1, l1["origins"], l1["delta"], res["phi0"], alpha, 1.0,
+                              tol=1e-12, max_sweeps=400000)
+    assert st1["status"] == O.OK, st1
+    assert rel(res["levels"][0]["phi"], ref1) < tol_rel
+    if len(l2["origins"]):
+        ref2, st2 = O.patch_solve(n0, 2, l2["origins"], l2["delta"], res["levels"][0]["phi"],
+                                  alpha, 1.0, parent_org=l1["origins"], tol=1e-12,
+                                  max_sweeps=400000)
+        assert st2["status"] == O.OK, st2
+        assert rel(res["levels"][1]["phi"], ref2) < tol_rel
+
+
+def test_high_density_union_matches_oracle():
+    """The refinement recipe at sigma 2 (patches over delta > 20, then > 80, 10 %
+    cell-scale noise) with r_V = 8 cells (alpha*kappa = 0.3): the level-1 density
+    reaches 138, alpha*kappa*delta ~ 41.  Both levels match the oracle's plain
+    Newton-Gauss-Seidel solution of the same system."""
+    h = I.refined_hierarchy(16, 2.0, 7)
+    assert [len(L["origins"]) for L in h["levels"]] == [22, 2]
+    alpha = I.alpha_kappa_for_rv(8.0)
+    res = solve_hierarchy(h, alpha=alpha, tol=1e-11)
+    assert res["stats"]["rc"] == mg.MG_OK, res["stats"]
+    _levels_vs_oracle(h, res, alpha, 1e-10)
+
+
+def test_union_where_the_rediscretised_correction_fails():
+    """32^3 at sigma 2 (170 level-1 and 16 level-2 patches, level-1 delta up to 274)
+    with alpha*kappa = 0.3: the FAS correction with the rediscretised coarse
+    operator makes the union residual grow, the Galerkin correction (the default)
+    converges, and the oracle's residual of every level is below the tolerance."""
+    h = I.refined_hierarchy(32, 2.0, 1303)
+    l1, l2 = h["levels"]
+    assert (len(l1["origins"]), len(l2["origins"])) == (170, 16)
+    alpha = I.alpha_kappa_for_rv(8.0)
+    tol = 1e-11
+    res = solve_hierarchy(h, alpha=alpha, tol=tol)
+    assert res["stats"]["rc"] == mg.MG_OK, (res["stats"], mg.mg_last_error())
+    _levels_vs_oracle(h, res, alpha, 1e-10)
+    d1, _ = O.patch_residual(32, 1, l1["origins"], res["levels"][0]["phi"], l1["delta"],
+                             res["phi0"], alpha, 1.0)
+    assert np.abs(d1).max() < tol
+    d2, _ = O.patch_residual(32, 2, l2["origins"], res["levels"][1]["phi"], l2["delta"],
+                             res["levels"][0]["phi"], alpha, 1.0, parent_org=l1["origins"])
+    assert np.abs(d2).max() < tol
+    fas = solve_hierarchy(h, alpha=alpha, tol=tol, patch_galerkin=0)
+    assert fas["stats"]["rc"] == mg.MG_ENOCONV

@@ -67,3 +67,36 @@ def test_noalloc_residual_rejects_sizes_beyond_its_storage():
                                   0, 0.3, 1.0)
     assert e.value.status == mg.MG_EINVAL
     assert "256" in mg.mg_last_error()
+
+
+@pytest.mark.parametrize("n", [256, 254])
+def test_noalloc_residual_at_and_below_its_capacity(n):
+    """n = 256 fills the fixed storage exactly (one partial per 256-cell block,
+    65,536 of them); n = 254 is the largest size below it."""
+    ref, new, d_ref, d_new = both(n, 31, I.alpha_kappa_for_rv(8.0), 1.0, 0, True, 1e-4)
+    check(ref, new, d_ref, d_new)
+
+
+def test_noalloc_residual_without_norms_still_writes_d():
+    """With a NULL norms pointer the call still completes the kernel before it
+    returns (it synchronises the stream) and writes d."""
+    n = 16
+    delta = I.lognormal_delta(n, 1.0, 41)
+    phi = 0.01 * I.random_field(n, 42)
+    d_ref = torch.empty((n, n, n), dtype=torch.float64, device="cuda:0")
+    d_new = torch.full((n, n, n), float("nan"), dtype=torch.float64, device="cuda:0")
+    mg.mg_op_residual(n, dev(phi), dev(delta), None, 0, 0.3, 1.0, d_ref)
+    assert mg.mg_op_residual_noalloc(n, dev(phi), dev(delta), None, 0, 0.3, 1.0, d_new,
+                                     want_norms=False) is None
+    scale = d_ref.abs().max().item() + 1.0
+    assert (d_new - d_ref).abs().max().item() <= 64 * EPS * scale
+
+
+@pytest.mark.parametrize("alpha", [float("nan"), float("inf")])
+def test_noalloc_residual_rejects_a_non_finite_alpha_like_the_allocating_one(alpha):
+    n = 8
+    z = torch.zeros((n, n, n), dtype=torch.float64, device="cuda:0")
+    for fn in (mg.mg_op_residual, mg.mg_op_residual_noalloc):
+        with pytest.raises(mg.MGError) as e:
+            fn(n, z, z, None, 0, alpha, 1.0)
+        assert e.value.status == mg.MG_EINVAL
