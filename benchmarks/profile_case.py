@@ -35,10 +35,15 @@ def main(argv=None):
                    help="run the six solves of one benchmark step (128^3 lognormal, "
                         "r_V = 2, 8, 32 cells, both signs) instead of a single solve")
     p.add_argument("--sweep32", type=int, default=0)
+    p.add_argument("--opt", default="",
+                   help="further options of the solve, 'name=value,...' (e.g. half32=1)")
+    p.add_argument("--reps", type=int, default=1, help="solves of the case (solve case)")
     p.add_argument("--galerkin", type=int, default=1,
                    help="coarse-grid correction of the refinement unions (c3 case)")
     p.add_argument("--alpha", type=float, default=None,
                    help="alpha*kappa of the c3 case (default r_V = 8 cells, 0.3)")
+    p.add_argument("--variants", default=None,
+                   help="';'-separated option sets 'k=v,k=v' tried one after another")
     p.add_argument("--case", choices=["solve", "refined", "batch", "particles", "c3"],
                    default="solve",
                    help="refined: a 128^3 sigma 2.0 domain with two refinement levels "
@@ -62,17 +67,32 @@ def main(argv=None):
         delta = torch.from_numpy(inputs.lognormal_delta(args.n, args.sigma, args.seed)).cuda()
         solves = [{"alpha": inputs.alpha_kappa_for_rv(args.rv), "kappa": 1.0, "branch": 0}]
         n = args.n
-    g = mg.mg_create_grid(n, mg.options(prec=prec, sweep32=args.sweep32))
+    extra = {}
+    for kv in filter(None, args.opt.split(",")):
+        k, v = kv.split("=")
+        extra[k] = float(v) if ("." in v or "e" in v) else int(v)
+    g = mg.mg_create_grid(n, mg.options(prec=prec, sweep32=args.sweep32, **extra))
     out = []
+    variants = [dict(kv.split("=") for kv in v.split(",") if kv)
+                for v in args.variants.split(";")] if args.variants else [{}]
     try:
         mg.mg_set_stream(g, torch.cuda.current_stream())
         mg.mg_set_density(g, 0, -1, delta)
         zero = torch.zeros_like(delta)
-        for s in solves:
-            mg.mg_set_field(g, 0, -1, zero)
-            st = mg.mg_solve(g, s["branch"], s["alpha"], s["kappa"], args.tol)
-            st.pop("hist", None)
-            out.append(st)
+        base = mg.mg_get_options(g)
+        for var in variants:
+            opt = mg.mg_get_options(g)
+            for k in mg.options_dict(base):
+                setattr(opt, k, getattr(base, k))
+            for k, v in var.items():
+                setattr(opt, k, float(v) if ("." in v or "e" in v) else int(v))
+            mg.mg_set_options(g, opt)
+            for s in solves * args.reps:
+                mg.mg_set_field(g, 0, -1, zero)
+                st = mg.mg_solve(g, s["branch"], s["alpha"], s["kappa"], args.tol, check=False)
+                st.pop("hist", None)
+                st["variant"] = var
+                out.append(st)
     finally:
         mg.mg_destroy_grid(g)
     for st in out:
@@ -94,18 +114,25 @@ def other_case(args, torch, inputs, mg):
                 mg.mg_add_patches(g, lvl, L["origins"])
                 mg.mg_set_density(g, lvl, -1, np.ascontiguousarray(L["delta"]))
             out = []
-            for rep in range(2):
+            variants = [dict(kv.split("=") for kv in v.split(",") if kv)
+                        for v in args.variants.split(";")] if args.variants else [{}, {}]
+            for rep, var in enumerate(variants):
+                opt = mg.mg_get_options(g)
+                for k, v in var.items():
+                    setattr(opt, k, type(getattr(opt, k))(float(v)) if "." in v or "e" in v
+                            else int(v))
+                mg.mg_set_options(g, opt)
                 zero = np.zeros_like(h["delta0"])
                 mg.mg_set_field(g, 0, -1, zero)
-                for lvl, L in enumerate(h["levels"], start=1):
-                    mg.mg_set_field(g, lvl, -1, np.zeros((len(L["origins"]), 8, 8, 8)))
+                for lvl in range(1, len(h["levels"]) + 1):
+                    mg.mg_set_field(g, lvl, -1, None)   # start from the level below
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 st = mg.mg_solve(g, 0, alpha, 1.0, args.tol, check=False)
                 torch.cuda.synchronize()
                 wall = time.perf_counter() - t0
                 lv = [mg.mg_get_level_stats(g, lvl) for lvl in (1, 2)]
-                out.append({"rep": rep, "rc": st["rc"], "wall_s": wall,
+                out.append({"rep": rep, "variant": var, "rc": st["rc"], "wall_s": wall,
                             "domain": {"cycles": st["cycles"], "wall_s": st["wall_s"]},
                             "levels": [{"cycles": s["cycles"], "status": s["status"],
                                         "res": s["res"], "wall_s": s["wall_s"],

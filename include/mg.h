@@ -54,7 +54,7 @@ typedef enum {
   MG_ECUDA = 3,    /* a CUDA call failed; see mg_last_error() */
   MG_ENOCONV = 4,  /* max_cycles reached, residual grew 1e3-fold, or stalled */
   MG_ENAN = 5,     /* a residual was not finite */
-  MG_ETIMEOUT = 6, /* a device-side wait ran out (reserved) */
+  MG_ETIMEOUT = 6, /* a kernel waited longer than barrier_timeout_s for its data */
   MG_ESTATE = 7    /* call out of order (e.g. solve before set_density) */
 } mg_status;
 
@@ -139,6 +139,14 @@ typedef struct {
                         0 uses the FAS coarse equations with the rediscretised operator.
                         The converged solution is the same; with alpha*kappa*delta >> 1
                         in dense regions only the Galerkin correction converges. */
+  int half32;        /* mixed precision, levels with n = 256 or 512: 1 runs each FP32
+                        correction sweep as two launches of two colours each, streaming
+                        planes of whole rows through shared memory with bulk asynchronous
+                        copies (same arithmetic, same bits as the per-colour launches);
+                        0 keeps four launches per sweep. */
+  double barrier_timeout_s; /* longest wait of a kernel for its asynchronous copies
+                        (default 1 s); a kernel that waits longer records the failure
+                        and returns, and the solve returns MG_ETIMEOUT */
 } mg_options;
 
 typedef struct {
@@ -198,7 +206,11 @@ mg_status mg_add_patches(mg_grid* g, int level, int count, const int32_t* origin
 mg_status mg_set_density(mg_grid* g, int level, int patch, const double* delta, int on_device);
 
 /* Set the field phi (initial guess, or a saved state to resume from); same
- * addressing as mg_set_density.  The field starts at zero otherwise. */
+ * addressing as mg_set_density.  The domain field starts at zero otherwise.  A
+ * refinement level that has no initial guess (never set, or reset by passing
+ * phi = NULL with patch = -1) starts its next solve from the cell-centred
+ * trilinear interpolation of the level below, as a new refinement inherits the
+ * coarse solution; after a solve its last iterate is the next initial guess. */
 mg_status mg_set_field(mg_grid* g, int level, int patch, const double* phi, int on_device);
 
 /*
@@ -209,7 +221,8 @@ mg_status mg_set_field(mg_grid* g, int level, int patch, const double* phi, int 
  * sgn(alpha), the physical root of Eq. one_branch.  With alpha = 0 the equation
  * is the linear Poisson equation and branch must be 0.  tol is in the units of
  * kappa*delta.  `stats` may be NULL; it describes the domain solve.
- * On MG_ENOCONV or MG_ENAN the last iterate stays in the handle.
+ * On MG_ENOCONV or MG_ENAN the last iterate stays in the handle; after
+ * MG_ETIMEOUT the field is undefined and must be set again before the next solve.
  * Errors: MG_EINVAL, MG_ESTATE (no density), MG_ENOCONV, MG_ENAN, MG_ECUDA.
  */
 mg_status mg_solve(mg_grid* g, int branch, double alpha, double kappa, double tol,
@@ -237,10 +250,12 @@ mg_status mg_set_options(mg_grid* g, const mg_options* opt);
 
 /*
  * Autotuner.  Solves the handle's problem (its density and the field the caller
- * left in it, restored before every trial) with every combination of
- * nu_pre, nu_post in {1,2,3}, fuse_coarse in {0,1} and, for MG_MIXED,
- * inner_cycles in {1,2,3,4}; each candidate is solved twice and timed on the
- * device (the second solve counts).  The fastest candidate that converges to
+ * left in it, restored before every trial) with every combination of a sweep
+ * pair (nu_pre, nu_post) from {1,1 2,1 1,2 2,2 3,2 2,3 3,3 4,3 3,4 4,4}, for
+ * MG_MIXED inner_cycles in {2,3,4} and (n = 256 or 512) half32 in {0,1}, and
+ * for n <= 64 fuse_coarse in {0,1}; each candidate is solved and timed on the
+ * device (twice for n <= 64, where the second solve counts).  The fastest
+ * candidate that converges to
  * `tol` becomes the handle's options and is returned in *best (may be NULL) with
  * its time in *best_seconds (may be NULL).  With a cache_path, the choice is
  * stored in that JSON file under the key "n=<n>,prec=<fp64|mixed>,device=<name>";

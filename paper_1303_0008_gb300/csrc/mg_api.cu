@@ -52,6 +52,8 @@ void mg_default_options(mg_options* opt) {
   opt->tau_stop = 0.0;
   opt->w = 1.0 / 3.0;
   opt->patch_galerkin = 1;
+  opt->half32 = 0;
+  opt->barrier_timeout_s = 1.0;
 }
 
 static mg_status check_options(const mg_options& o) {
@@ -78,6 +80,9 @@ static mg_status check_options(const mg_options& o) {
   if (!(o.tau_stop >= 0.0 && o.tau_stop < 1e3)) MG_FAIL(MG_EINVAL, "options: tau_stop");
   if (!(o.w >= 0.0 && o.w < 1.0)) MG_FAIL(MG_EINVAL, "options: w");
   if (o.patch_galerkin != 0 && o.patch_galerkin != 1) MG_FAIL(MG_EINVAL, "options: patch_galerkin");
+  if (o.half32 != 0 && o.half32 != 1) MG_FAIL(MG_EINVAL, "options: half32");
+  if (!(o.barrier_timeout_s >= 0.0 && o.barrier_timeout_s <= 3600.0))
+    MG_FAIL(MG_EINVAL, "options: barrier_timeout_s must be in [0, 3600]");
   return MG_OK;
 }
 
@@ -281,6 +286,18 @@ mg_status mg_set_field(mg_grid* g, int level, int patch, const double* phi, int 
   size_t cnt;
   mg_status st = resolve(g, level, patch, true, &dst, &cnt);
   if (st != MG_OK) return st;
+  if (level > 0 && !g->batch) {
+    PatchLevel* pl = g->patch_levels[level - 1];
+    if (!phi) {
+      // no values: the next solve starts the level from the level below
+      if (patch != -1) MG_FAIL(MG_EINVAL, "mg_set_field: NULL phi resets a whole level (patch -1)");
+      pl->phi_set = false;
+      return MG_OK;
+    }
+    st = copy_in(g, dst, phi, cnt, on_device);
+    if (st == MG_OK) pl->phi_set = true;
+    return st;
+  }
   return copy_in(g, dst, phi, cnt, on_device);
 }
 
@@ -371,7 +388,8 @@ mg_status mg_solve(mg_grid* g, int branch, double alpha, double kappa, double to
     PatchLevel* pl = g->patch_levels[l];
     if (!pl || pl->count == 0) continue;
     if (!pl->density_set) MG_FAIL(MG_ESTATE, "mg_solve: patch density not set");
-    mg_status ps = patch_level_solve(g, (int)l + 1, branch, alpha, kappa, tol);
+    mg_status ps = patch_level_solve(g, (int)l + 1, branch, alpha, kappa, tol, !pl->phi_set);
+    pl->phi_set = true;  // the last iterate is the next solve's initial guess
     if (ps != MG_OK) return ps;
   }
   return MG_OK;

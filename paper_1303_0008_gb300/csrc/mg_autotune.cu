@@ -1,7 +1,8 @@
 // Autotuner: pick the sweep counts (and, for the mixed path, the inner V-cycles
-// per FP64 correction) that give the shortest time to the requested residual on
-// the handle's own problem, and remember the choice in a small JSON file keyed by
-// grid size, precision and device name.
+// per FP64 correction and the shape of the FP32 sweep: four colour launches or
+// two half sweeps over tiles of whole rows) that give the shortest time to the
+// requested residual on the handle's own problem, and remember the choice in a
+// small JSON file keyed by grid size, precision and device name.
 //
 // Each trial restores the field the caller left in the handle, solves with one
 // candidate, and reads the device time of the solve (CUDA events).  Candidates
@@ -123,6 +124,7 @@ extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double ka
     o.nu_post = (int)e.at("nu_post");
     o.inner_cycles = (int)e.at("inner_cycles");
     o.fuse_coarse = (int)e.at("fuse_coarse");
+    if (e.count("half32")) o.half32 = (int)e.at("half32");
     g->opt = o;
     if (best) *best = o;
     if (best_seconds) *best_seconds = e.count("seconds") ? e.at("seconds") : -1.0;
@@ -137,26 +139,40 @@ extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double ka
   }
   cudaMemcpyAsync(saved, d->lv[0].phi, bytes, cudaMemcpyDeviceToDevice, g->stream);
   const mg_options base = g->opt;
+  // Candidates: pre/post sweep pairs up to 4 that differ by at most one (the
+  // strongly nonlinear workloads want more smoothing than the 2/2 default); for
+  // the mixed path 2, 3 or 4 inner V-cycles per FP64 correction and, where the
+  // grid supports it, the FP32 sweep as four colour launches or two half sweeps;
+  // the coarse-level fusion only where it matters (n <= 64).
   std::vector<mg_options> cands;
-  const int inner_set[] = {1, 2, 3, 4};
-  for (int pre = 1; pre <= 3; ++pre)
-    for (int post = 1; post <= 3; ++post)
-      for (int ic = 0; ic < (base.prec == MG_MIXED ? 4 : 1); ++ic)
-        for (int fuse = 0; fuse <= 1; ++fuse) {
+  const int pairs[][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 2}, {2, 3},
+                          {3, 3}, {4, 3}, {3, 4}, {4, 4}};
+  const bool mixed = base.prec == MG_MIXED;
+  const int inner_set[] = {2, 3, 4};
+  const bool half_ok = mixed && half_sweep_supported(d->n);
+  const bool fuse_matters = d->n <= 64;
+  for (const auto& pp : pairs)
+    for (int ic = 0; ic < (mixed ? 3 : 1); ++ic)
+      for (int half = 0; half <= (half_ok ? 1 : 0); ++half)
+        for (int fuse = 0; fuse <= (fuse_matters ? 1 : 0); ++fuse) {
           mg_options o = base;
-          o.nu_pre = pre;
-          o.nu_post = post;
-          o.inner_cycles = base.prec == MG_MIXED ? inner_set[ic] : base.inner_cycles;
-          o.fuse_coarse = fuse;
+          o.nu_pre = pp[0];
+          o.nu_post = pp[1];
+          o.inner_cycles = mixed ? inner_set[ic] : base.inner_cycles;
+          o.half32 = half_ok ? half : base.half32;
+          o.fuse_coarse = fuse_matters ? fuse : base.fuse_coarse;
           cands.push_back(o);
         }
+  // small grids: two solves per candidate (the first also captures the graphs and
+  // is noisier); from 128^3 on a solve is long enough to time once
+  const int reps = d->n <= 64 ? 2 : 1;
   double t_best = 1e300;
   mg_options o_best = base;
   mg_status result = MG_ENOCONV;
   for (const mg_options& o : cands) {
     double t = 0.0;
     bool ok = true;
-    for (int rep = 0; rep < 2 && ok; ++rep) {  // the first solve also captures graphs
+    for (int rep = 0; rep < reps && ok; ++rep) {
       cudaMemcpyAsync(d->lv[0].phi, saved, bytes, cudaMemcpyDeviceToDevice, g->stream);
       mg_solve_stats st;
       const mg_status s = domain_solve(d, o, g->stream, branch, alpha, kappa, tol, &st);
@@ -184,6 +200,7 @@ extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double ka
                   {"nu_post", (double)o_best.nu_post},
                   {"inner_cycles", (double)o_best.inner_cycles},
                   {"fuse_coarse", (double)o_best.fuse_coarse},
+                  {"half32", (double)o_best.half32},
                   {"seconds", t_best}};
     if (!write_cache(cache_path, cache)) {
       set_error("mg_autotune: cannot write the cache file");

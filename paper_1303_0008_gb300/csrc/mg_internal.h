@@ -211,6 +211,17 @@ void launch_subcycle64(cudaStream_t st, const SubCycleArgs& a);
 void launch_subcycle32(cudaStream_t st, const SubCycleArgs& a);
 void init_subcycle();
 
+// Two-launch four-colour sweep of the FP32 correction operator (mg_halfsweep32.cu):
+// colours 0 and 1, then 2 and 3, each launch streaming planes of whole rows
+// through shared memory with bulk asynchronous copies; e_in -> e_out, n = 256 or
+// 512.  *err is set when a copy does not arrive within limit_s seconds.
+bool half_sweep_supported(int n);
+void init_half32();
+void launch_half_sweep32(cudaStream_t st, int n, const float* e_in, float* e_out,
+                         const float* phi0, const float* q0, const float* g,
+                         const LevelScalars* sc, const OpConst32& c, int* err, double limit_s,
+                         EventPairs* timer = nullptr);
+
 // One-launch four-colour sweep of the FP32 correction operator (mg_sweep32.cu):
 // reads e_in, writes every cell of e_out; n >= 32 and n % 4 == 0.
 bool sweep32_eligible(int n);

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "mg_internal.h"
@@ -208,6 +209,9 @@ void mixed_release(Domain* d) {
     cudaFree(L.e2);
     L.e = L.ehat = L.phi0 = L.q0 = L.rhs = L.src32 = L.e2 = nullptr;
   }
+  cudaFree(d->d_flags);
+  if (d->h_flags) cudaFreeHost(d->h_flags);
+  d->d_flags = d->h_flags = nullptr;
   d->mixed_ready = false;
 }
 
@@ -224,6 +228,9 @@ static mg_status mixed_prepare(Domain* d) {
     if (l > 0) ok = ok && cudaMalloc(&L.ehat, b) == cudaSuccess;
     if (sweep32_eligible(L.n)) ok = ok && cudaMalloc(&L.e2, b) == cudaSuccess;
   }
+  ok = ok && cudaMalloc(&d->d_flags, 4 * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&d->h_flags, 4 * sizeof(int)) == cudaSuccess;
+  if (ok) ok = cudaMemset(d->d_flags, 0, 4 * sizeof(int)) == cudaSuccess;
   if (!ok) {
     mixed_release(d);
     set_error("device allocation failed (mixed precision arrays)");
@@ -236,6 +243,7 @@ static mg_status mixed_prepare(Domain* d) {
     attr = true;
   }
   init_sweep32();
+  init_half32();
   d->mixed_ready = true;
   return MG_OK;
 }
@@ -256,6 +264,22 @@ struct CycleMixed {
 
   void smooth(int l, int sweeps) const {
     Level& L = d->lv[l];
+    if (o->half32 && L.e2 && half_sweep_supported(L.n)) {
+      // each sweep as two half sweeps e -> e2 (or back); an odd count ends in e2
+      // and is copied back
+      EventPairs* t = (l == 0 && timer && timer->enabled) ? timer : nullptr;
+      float* cur = L.e;
+      float* nxt = L.e2;
+      for (int s = 0; s < sweeps; ++s) {
+        const bool timed = t && (!t->first_only || s == 0);
+        launch_half_sweep32(st, L.n, cur, nxt, L.phi0, L.q0, L.rhs, sc32(l), ops32[l],
+                            d->d_flags, o->barrier_timeout_s, timed ? t : nullptr);
+        std::swap(cur, nxt);
+      }
+      if (cur != L.e)
+        cudaMemcpyAsync(L.e, cur, sizeof(float) * (size_t)L.cells, cudaMemcpyDeviceToDevice, st);
+      return;
+    }
     if (o->sweep32 && L.e2) {
       // pairs of one-launch sweeps e -> e2 -> e; an odd last sweep goes e -> e2
       // and is copied back
@@ -381,6 +405,7 @@ struct CycleMixed {
     count_launches(1);
     launch_finalize(st, d->d_part, (int)nb, (double)L.cells, 1, d->d_sc);
     cudaMemcpyAsync(d->h_sc, d->d_sc, sizeof(LevelScalars), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(d->h_flags, d->d_flags, sizeof(int), cudaMemcpyDeviceToHost, st);
   }
 
   // Coarse copies of the expansion point, the inner V-cycles, phi += e.
@@ -409,8 +434,10 @@ mg_status mixed_solve(Domain* d, const mg_options& o, cudaStream_t st, const OpC
   for (int l = 0; l < d->nlev; ++l) ops32[l] = make_op32(d->lv[l].n, alpha, branch);
   // the finest FP32 colour stages are timed when they run as per-colour launches
   EventPairs tb;
-  tb.enabled = o.time_kernels != 0 && !o.sweep32 && !o.pair32;
+  const bool half = o.half32 && half_sweep_supported(d->lv[0].n);
+  tb.enabled = o.time_kernels != 0 && (half || (!o.sweep32 && !o.pair32));
   tb.first_only = o.time_kernels == 2;
+  MCK(cudaMemsetAsync(d->d_flags, 0, sizeof(int), st));
   CycleMixed cyc{d, &o, st, ops, ops32.data(), (float)kappa, o.guard == MG_GUARD_FLOOR, &tb};
   domain_invalidate_graphs(d);
   long long na = 0, nb = 0;
@@ -422,7 +449,8 @@ mg_status mixed_solve(Domain* d, const mg_options& o, cudaStream_t st, const OpC
   }
   const bool graphs = o.use_graphs && d->gexec[2] && d->gexec[3];
   const int pairs_b = tb.n;
-  const double cells_per_launch = (double)d->lv[0].cells / 4.0;
+  // a timed launch is one colour stage, or with half sweeps one half sweep
+  const double cells_per_launch = (double)d->lv[0].cells / (half ? 2.0 : 4.0);
   bool b_pending = false;
   auto harvest = [&]() {
     if (!tb.enabled || !b_pending) return;
@@ -448,6 +476,11 @@ mg_status mixed_solve(Domain* d, const mg_options& o, cudaStream_t st, const OpC
     MCK(cudaStreamSynchronize(st));
     MCK(cudaGetLastError());
     harvest();
+    if (d->h_flags[0]) {
+      set_error("an FP32 half sweep waited longer than barrier_timeout_s for its data");
+      result = MG_ETIMEOUT;
+      break;
+    }
     const double res = d->h_sc[0].res;
     s->outer += 1;
     s->guard_hits = o.guard == MG_GUARD_FLOOR ? (long long)d->h_sc[0].floored

@@ -249,6 +249,28 @@ __global__ void __launch_bounds__(128) k_patch_ghosts(const int* __restrict__ or
   }
 }
 
+// Initial guess of a refinement level: every patch cell takes the cell-centred
+// trilinear interpolation of the parent level (the values the coarse-to-fine
+// fill gives its ghost cells), as a new refinement inherits the coarse solution.
+__global__ void __launch_bounds__(128) k_patch_init(const int* __restrict__ origin, FieldSrc src,
+                                                    double* __restrict__ phi) {
+  const int p = blockIdx.x;
+  const int ox0 = origin[3 * p], oy0 = origin[3 * p + 1], oz0 = origin[3 * p + 2];
+  for (int t = threadIdx.x; t < 512; t += blockDim.x) {
+    const int x = ox0 + (t & 7), y = oy0 + ((t >> 3) & 7), z = oz0 + (t >> 6);
+    const int X = x >> 1, Y = y >> 1, Z = z >> 1;
+    const int sX = (x & 1) ? 1 : -1, sY = (y & 1) ? 1 : -1, sZ = (z & 1) ? 1 : -1;
+    double v = 0.0;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        for (int cc = 0; cc < 2; ++cc) {
+          const double wt = (a ? 0.25 : 0.75) * (b ? 0.25 : 0.75) * (cc ? 0.25 : 0.75);
+          v += wt * fetch(src, X + a * sX, Y + b * sY, Z + cc * sZ);
+        }
+    phi[(long long)p * 512 + t] = v;
+  }
+}
+
 // Mean of the 8 children within each patch (block B -> B/2).
 template <int B>
 __global__ void __launch_bounds__(128) k_patch_restrict(const double* __restrict__ fine,
@@ -542,7 +564,7 @@ static FieldSrc dense_src(const double* a, int n, int* err) {
 }
 
 mg_status patch_level_solve(mg_grid* g, int level, int branch, double alpha, double kappa,
-                            double tol) {
+                            double tol, bool init_from_parent) {
   PatchLevel* pl = g->patch_levels[level - 1];
   cudaStream_t st = g->stream;
   const int P = pl->count;
@@ -567,6 +589,10 @@ mg_status patch_level_solve(mg_grid* g, int level, int branch, double alpha, dou
       level == 1 ? dense_src(d0->lv[0].phi, n0, pl->d_err)
                  : FieldSrc{nullptr, parent->nside, parent->phi, parent->d_table, pl->d_err};
   k_patch_ghosts<8><<<P, 128, 0, st>>>(pl->d_origin, pl->d_nbr, 0, parent_src, pl->ghost);
+  if (init_from_parent) {
+    k_patch_init<<<P, 128, 0, st>>>(pl->d_origin, parent_src, pl->phi);
+    count_launches(1);
+  }
   // union level m sits on level (level - m): level 0 dense, level 1 patches, or the
   // domain restricted once (m = 2 of level 1)
   for (int m = 1; m < 3; ++m) {

@@ -44,6 +44,10 @@ struct Domain {
   unsigned char* d_subguard = nullptr;
   bool density_set = false;
   bool mixed_ready = false;
+  // error flags of kernels that wait on asynchronous copies ([0]: a copy did not
+  // arrive within barrier_timeout_s), and their pinned host mirror
+  int* d_flags = nullptr;
+  int* h_flags = nullptr;
   // CUDA graphs of the two halves of a V-cycle (captured per solve)
   cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
 };
@@ -54,6 +58,7 @@ struct PatchLevel {
   int count = 0;
   int nside = 0;       // cells per side of this level's periodic index space
   bool density_set = false;
+  bool phi_set = false;       // phi holds an initial guess (set by the caller or a solve)
   int* d_origin = nullptr;    // 3 * count
   int* d_nbr = nullptr;       // 27 * count: neighbour patch index or -1
   double* phi = nullptr;      // count * 512
@@ -123,8 +128,10 @@ int num_levels(int n, int coarsest);
 // mg_patch.cu
 mg_status patches_add(mg_grid* g, int level, int count, const int* origin);
 void patch_level_destroy(PatchLevel* pl);
+// init_from_parent: start from the trilinear interpolation of the level below
+// instead of the field held by the level.
 mg_status patch_level_solve(mg_grid* g, int level, int branch, double alpha, double kappa,
-                            double tol);
+                            double tol, bool init_from_parent = false);
 mg_status patch_force(mg_grid* g, int level, int patch, double* out);
 void patch_restrict_density(mg_grid* g, PatchLevel* pl);
 

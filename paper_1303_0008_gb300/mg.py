@@ -40,7 +40,8 @@ class mg_options(ctypes.Structure):
                 ("patch_mg_levels", ctypes.c_int), ("patch_cgc", ctypes.c_double),
                 ("sweep32", ctypes.c_int), ("pair32", ctypes.c_int),
                 ("tau_stop", ctypes.c_double), ("w", ctypes.c_double),
-                ("patch_galerkin", ctypes.c_int)]
+                ("patch_galerkin", ctypes.c_int), ("half32", ctypes.c_int),
+                ("barrier_timeout_s", ctypes.c_double)]
 
 
 class mg_solve_stats(ctypes.Structure):
@@ -210,6 +211,11 @@ def mg_set_density(g, level: int, patch: int, delta):
 
 
 def mg_set_field(g, level: int, patch: int, phi):
+    """phi = None (refinement levels, patch -1): the next solve starts the level
+    from the interpolation of the level below."""
+    if phi is None:
+        _check(lib().mg_set_field(g, level, patch, None, 0), "mg_set_field")
+        return
     p, dev, _ = _arr(phi)
     _check(lib().mg_set_field(g, level, patch, p, dev), "mg_set_field")
 

@@ -46,7 +46,7 @@ def test_single_process_aggregation_is_identity():
     assert bench.max_over_ranks(3.5) == 3.5 and bench.sum_over_ranks(6.0) == 6.0
 
 
-@pytest.mark.parametrize("kernel", ["k_smooth_colour64", "k_smooth_colour32_n"])
+@pytest.mark.parametrize("kernel", ["k_smooth_colour64", "k_smooth_colour32_n", "k_half32"])
 def test_traffic_record_matches_the_smoother_source(kernel):
     """The benchmark's DRAM-traffic figures are tied to a hash of each roofline
     kernel's source (the headers of its body, the kernel and its launcher).  The

@@ -25,7 +25,7 @@ def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-def solve_hierarchy(h, alpha=ALPHA, kappa=1.0, tol=1e-11, **opt):
+def solve_hierarchy(h, alpha=ALPHA, kappa=1.0, tol=1e-11, zero_start=False, **opt):
     n0 = h["delta0"].shape[0]
     g = mg.mg_create_grid(n0, mg.options(**opt))
     out = {"levels": []}
@@ -36,6 +36,8 @@ def solve_hierarchy(h, alpha=ALPHA, kappa=1.0, tol=1e-11, **opt):
                 continue
             mg.mg_add_patches(g, lvl, L["origins"])
             mg.mg_set_density(g, lvl, -1, np.ascontiguousarray(L["delta"]))
+            if zero_start:
+                mg.mg_set_field(g, lvl, -1, np.zeros((len(L["origins"]), 8, 8, 8)))
         out["stats"] = mg.mg_solve(g, 0, alpha, kappa, tol, check=False)
         phi0 = np.empty_like(h["delta0"])
         mg.mg_get_field(g, 0, -1, phi0)
@@ -187,9 +189,11 @@ def test_high_density_union_matches_oracle():
 
 def test_union_where_the_rediscretised_correction_fails():
     """32^3 at sigma 2 (170 level-1 and 16 level-2 patches, level-1 delta up to 274)
-    with alpha*kappa = 0.3: the FAS correction with the rediscretised coarse
-    operator makes the union residual grow, the Galerkin correction (the default)
-    converges, and the oracle's residual of every level is below the tolerance."""
+    with alpha*kappa = 0.3.  From the default initial guess (the interpolation of
+    the level below) the Galerkin correction converges to the oracle's solution of
+    each level.  From a zero initial guess the FAS correction with the
+    rediscretised coarse operator makes the union residual grow, while the
+    Galerkin correction still converges."""
     h = I.refined_hierarchy(32, 2.0, 1303)
     l1, l2 = h["levels"]
     assert (len(l1["origins"]), len(l2["origins"])) == (170, 16)
@@ -204,5 +208,45 @@ def test_union_where_the_rediscretised_correction_fails():
     d2, _ = O.patch_residual(32, 2, l2["origins"], res["levels"][1]["phi"], l2["delta"],
                              res["levels"][0]["phi"], alpha, 1.0, parent_org=l1["origins"])
     assert np.abs(d2).max() < tol
-    fas = solve_hierarchy(h, alpha=alpha, tol=tol, patch_galerkin=0)
-    assert fas["stats"]["rc"] == mg.MG_ENOCONV
+    gal0 = solve_hierarchy(h, alpha=alpha, tol=tol, zero_start=True)
+    assert gal0["stats"]["rc"] == mg.MG_OK
+    assert rel(gal0["levels"][0]["phi"], res["levels"][0]["phi"]) < 1e-10
+    fas0 = solve_hierarchy(h, alpha=alpha, tol=tol, zero_start=True, patch_galerkin=0)
+    assert fas0["stats"]["rc"] == mg.MG_ENOCONV
+
+
+def test_level_initial_guess_and_reset(small):
+    """A refinement level without an initial guess starts from the interpolation of
+    the level below; after a solve its last iterate is kept, and passing NULL for
+    the whole level (patch -1) resets it.  Every start reaches the same solution."""
+    h = small
+    n0 = h["delta0"].shape[0]
+    g = mg.mg_create_grid(n0)
+    try:
+        mg.mg_set_density(g, 0, -1, h["delta0"])
+        for lvl, L in enumerate(h["levels"], start=1):
+            mg.mg_add_patches(g, lvl, L["origins"])
+            mg.mg_set_density(g, lvl, -1, np.ascontiguousarray(L["delta"]))
+        mg.mg_solve(g, 0, ALPHA, 1.0, 1e-11)
+        first = mg.mg_get_level_stats(g, 1)
+        a = np.empty((len(h["levels"][0]["origins"]), 8, 8, 8))
+        mg.mg_get_field(g, 1, -1, a)
+        mg.mg_solve(g, 0, ALPHA, 1.0, 1e-11)      # resumes from the converged field
+        assert mg.mg_get_level_stats(g, 1)["cycles"] <= 1
+        mg.mg_set_field(g, 1, -1, None)           # start over from the level below
+        mg.mg_set_field(g, 2, -1, None)
+        mg.mg_solve(g, 0, ALPHA, 1.0, 1e-11)
+        again = mg.mg_get_level_stats(g, 1)
+        assert again["hist"][0] == pytest.approx(first["hist"][0], rel=1e-6)
+        b = np.empty_like(a)
+        mg.mg_get_field(g, 1, -1, b)
+        assert rel(b, a) < 1e-10
+        mg.mg_set_field(g, 1, -1, np.zeros_like(a))   # an explicit (zero) initial guess
+        mg.mg_solve(g, 0, ALPHA, 1.0, 1e-11)
+        mg.mg_get_field(g, 1, -1, b)
+        assert rel(b, a) < 1e-10
+        with pytest.raises(mg.MGError) as e:
+            mg.mg_set_field(g, 1, 0, None)            # NULL resets whole levels only
+        assert e.value.status == mg.MG_EINVAL
+    finally:
+        mg.mg_destroy_grid(g)
