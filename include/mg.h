@@ -252,7 +252,7 @@ mg_status mg_set_options(mg_grid* g, const mg_options* opt);
  * Autotuner.  Solves the handle's problem (its density and the field the caller
  * left in it, restored before every trial) with every combination of a sweep
  * pair (nu_pre, nu_post) from {1,1 2,1 1,2 2,2 3,2 2,3 3,3 4,3 3,4 4,4}, for
- * MG_MIXED inner_cycles in {2,3,4} and (n = 256 or 512) half32 in {0,1}, and
+ * MG_MIXED inner_cycles in {3,4} and (n = 256 or 512) half32 in {0,1}, and
  * for n <= 64 fuse_coarse in {0,1}; each candidate is solved and timed on the
  * device (twice for n <= 64, where the second solve counts).  The fastest
  * candidate that converges to

@@ -141,18 +141,18 @@ extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double ka
   const mg_options base = g->opt;
   // Candidates: pre/post sweep pairs up to 4 that differ by at most one (the
   // strongly nonlinear workloads want more smoothing than the 2/2 default); for
-  // the mixed path 2, 3 or 4 inner V-cycles per FP64 correction and, where the
+  // the mixed path 3 or 4 inner V-cycles per FP64 correction and, where the
   // grid supports it, the FP32 sweep as four colour launches or two half sweeps;
   // the coarse-level fusion only where it matters (n <= 64).
   std::vector<mg_options> cands;
   const int pairs[][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 2}, {2, 3},
                           {3, 3}, {4, 3}, {3, 4}, {4, 4}};
   const bool mixed = base.prec == MG_MIXED;
-  const int inner_set[] = {2, 3, 4};
+  const int inner_set[] = {3, 4};
   const bool half_ok = mixed && half_sweep_supported(d->n);
   const bool fuse_matters = d->n <= 64;
   for (const auto& pp : pairs)
-    for (int ic = 0; ic < (mixed ? 3 : 1); ++ic)
+    for (int ic = 0; ic < (mixed ? 2 : 1); ++ic)
       for (int half = 0; half <= (half_ok ? 1 : 0); ++half)
         for (int fuse = 0; fuse <= (fuse_matters ? 1 : 0); ++fuse) {
           mg_options o = base;
