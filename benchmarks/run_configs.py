@@ -4,7 +4,7 @@
 
 C1  32^3 top-hat (delta 10 in radius 4 cells), r_V = 8 cells, FP64
 C2  128^3 lognormal (sigma 1.5), r_V = 2, 8, 32 cells x both signs, FP64
-C3  256^3 lognormal + 8^3 patches over delta > 20 (then > 80): sigma 2.0 at alpha*kappa = 1e-3
+C3  256^3 lognormal + 8^3 patches over delta > 20 (then > 80): sigma 2.0 and 1.0 at r_V = 8 cells
     and sigma 1.0 at r_V = 8 cells, FP64
 C4  512^3 lognormal (sigma 2.0), r_V = 16 cells: mixed vs FP64
 C5  64 independent solves of 32..128^3, mixed, batched
@@ -81,7 +81,7 @@ def c3(mg, I, reps):
     import numpy as np
     import torch
     res = {"config": "C3", "variants": []}
-    for sigma, alpha in ((2.0, 1e-3), (1.0, I.alpha_kappa_for_rv(8.0))):
+    for sigma, alpha in ((2.0, I.alpha_kappa_for_rv(8.0)), (1.0, I.alpha_kappa_for_rv(8.0))):
         h = I.refined_hierarchy(256, sigma, 1303)
         levels = [L for L in h["levels"] if len(L["origins"])]
         g = mg.mg_create_grid(256, mg.options())
@@ -101,6 +101,8 @@ def c3(mg, I, reps):
             v["domain_cycles"] = st["cycles"]
             v["level_cycles"] = [mg.mg_get_level_stats(g, lvl)["cycles"]
                                  for lvl in range(1, len(levels) + 1)]
+            v["level_ms"] = [1e3 * mg.mg_get_level_stats(g, lvl)["wall_s"]
+                             for lvl in range(1, len(levels) + 1)]
         finally:
             mg.mg_destroy_grid(g)
         res["variants"].append(v)

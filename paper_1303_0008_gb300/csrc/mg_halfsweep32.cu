@@ -256,9 +256,11 @@ __global__ void __launch_bounds__(hsw::threads<N>()) k_half32(HalfArgs a) {
   // Wait for raw plane q, split its rows by x parity into compute slot q % SPLIT,
   // and send raw plane q + RAW into the freed raw slot.  false: the wait ran out.
   auto advance = [&](int q) -> bool {
-    const bool ok = __syncthreads_and(
-        mbar_wait(smem_u32(&bar[q % RAW]), (unsigned)((q / RAW) & 1), a.limit_ns));
-    if (!ok) return false;
+    // one warp polls the barrier; the others wait at the block barrier, which
+    // costs them no issue slots
+    const bool arrived =
+        tid >= 32 || mbar_wait(smem_u32(&bar[q % RAW]), (unsigned)((q / RAW) & 1), a.limit_ns);
+    if (!__syncthreads_and(arrived)) return false;
     constexpr int V = SLOT / 4;  // float4 per array
     for (int v = tid; v < 2 * V; v += NT) {
       const bool arr = v >= V;
