@@ -172,7 +172,7 @@ def _definition(text: str, head: str) -> str:
 # and the definitions (kernel, launcher, block-size rule) in its translation unit
 _KERNEL_SOURCES = {
     "k_half32": (("mg_bodies32.cuh", "mg_common.cuh"), "mg_halfsweep32.cu",
-                 ("__global__ void __launch_bounds__(hsw::THREADS, 1) k_half32(",
+                 ("__global__ void __launch_bounds__(hsw::threads<N>()) k_half32(",
                   "void launch_half_sweep32(")),
     "k_smooth_colour64": (("mg_bodies64.cuh", "mg_common.cuh"), "mg_fp64.cu",
                           ("__global__ void __launch_bounds__(256) k_smooth_colour64(",

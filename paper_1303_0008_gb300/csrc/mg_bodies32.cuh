@@ -84,11 +84,23 @@ __device__ __forceinline__ float2 dD2(const Stencil2& se, const Stencil2& sp, fl
 // inner problem.  Each thread takes kHandoffCells cells (a block covers
 // 256 kHandoffCells consecutive cells, coalesced per step), so the block's norm
 // reduction, about 15 FP64 warp instructions, is shared by several cells.
+// Index of cell (i,j,k) of an n^3 grid in colour order: the cells of colour
+// c = ((i+k)&1) + 2((j+k)&1) fill block c of n^3/4 entries, in the order in which
+// the threads of a colour stage visit them (x fastest, then y, then z), so that a
+// colour stage reads its own cells' values contiguously.
+__device__ __forceinline__ long long colour_index(int i, int j, int k, int n) {
+  const int colour = ((i + k) & 1) + 2 * ((j + k) & 1);
+  const long long hn = n >> 1;
+  return colour * (hn * hn * n) + ((long long)k * hn + (j >> 1)) * hn + (i >> 1);
+}
+
+// With q0c / gc (may be null) the hand-off also stores q0 and g in colour order
+// (colour_index) for the colour stages of the finest level.
 __device__ __forceinline__ void b_residual_handoff64(
     int n, const double* __restrict__ phi, const double* __restrict__ src, OpConst64 c,
     const LevelScalars* __restrict__ sc, float* __restrict__ g, float* __restrict__ q0,
     float* __restrict__ phi0, float* __restrict__ e, Partial* __restrict__ partials,
-    long long blk) {
+    long long blk, float* __restrict__ gc = nullptr, float* __restrict__ q0c = nullptr) {
   const long long cells = (long long)n * n * n;
   Partial p;
   partial_init(p);
@@ -125,6 +137,11 @@ __device__ __forceinline__ void b_residual_handoff64(
     q0[t] = (float)q;
     phi0[t] = (float)ctr;
     e[t] = 0.f;
+    if (gc) {
+      const long long ci = colour_index(i, j, k, n);
+      gc[ci] = (float)(lam - d);
+      q0c[ci] = (float)q;
+    }
   }
   p = block_reduce(p);
   if (threadIdx.x == 0) partials[blk] = p;
@@ -178,6 +195,18 @@ __device__ __forceinline__ void b_q0_prep32(int n, const float* __restrict__ phi
 
 // One cell of an FP32 colour stage: t indexes the colour's n^3/4 cells; t >= n^3/4
 // does nothing.  mu is the level's lambda in FP32.
+// The update of cell (i,j,k) (linear index id) given its q0 and g.
+__device__ __forceinline__ void cell_smooth32_at(int n, float* __restrict__ e,
+                                                 const float* __restrict__ phi0, float q0v,
+                                                 float gv, float mu, const OpConst32& c, int i,
+                                                 int j, int k, long long id) {
+  const NbrOff o = nbr_offsets(i, j, k, n);
+  const StencilT<float> se = gather_at(e + id, o);
+  float dd = 0.f;
+  if (!c.linear) dd = dD32(se, gather_at(phi0 + id, o), q0v, c);
+  e[id] = gs_value32(se, dd, gv, mu, c);
+}
+
 __device__ __forceinline__ void cell_smooth32(int n, float* __restrict__ e,
                                               const float* __restrict__ phi0,
                                               const float* __restrict__ q0,
@@ -191,11 +220,7 @@ __device__ __forceinline__ void cell_smooth32(int n, float* __restrict__ e,
   const int i = 2 * m + ((colour ^ k) & 1);
   const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
   const long long id = lidx(i, j, k, n);
-  const NbrOff o = nbr_offsets(i, j, k, n);
-  const StencilT<float> se = gather_at(e + id, o);
-  float dd = 0.f;
-  if (!c.linear) dd = dD32(se, gather_at(phi0 + id, o), q0[id], c);
-  e[id] = gs_value32(se, dd, g[id], mu, c);
+  cell_smooth32_at(n, e, phi0, q0[id], g[id], mu, c, i, j, k, id);
 }
 
 // Face sums and cross differences around c0 for a side N known at compile time and
@@ -220,7 +245,10 @@ __device__ __forceinline__ StencilT<float> gather_n(const float* c0, const float
 // cells share their row, and the y/z-boundary test below is uniform per warp).
 // Rows on a y or z boundary take the general path; the others address their
 // neighbours with immediates.  The arithmetic is cell_smooth32's, so the bits are.
-template <int N>
+// With CO, q0 and g arrive in colour order (colour_index): q0 and g point at this
+// colour's block, whose entry t is the cell the thread with index t updates, so a
+// warp reads them contiguously; otherwise they are the natural n^3 arrays.
+template <int N, bool CO>
 __device__ __forceinline__ void cell_smooth32_n(float* __restrict__ e,
                                                 const float* __restrict__ phi0,
                                                 const float* __restrict__ q0,
@@ -234,20 +262,21 @@ __device__ __forceinline__ void cell_smooth32_n(float* __restrict__ e,
   const int m = (int)(u % HN), jj = (int)((u / HN) % HN), k = (int)(u / (HN * HN));
   const int i = 2 * m + ((colour ^ k) & 1);
   const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
+  const long long id = (long long)i + (long long)N * (j + (long long)N * k);
+  const float q0v = CO ? q0[t] : q0[id], gv = CO ? g[t] : g[id];
   if (j == 0 || j == N - 1 || k == 0 || k == N - 1) {
-    cell_smooth32(N, e, phi0, q0, g, mu, c, colour, t);
+    cell_smooth32_at(N, e, phi0, q0v, gv, mu, c, i, j, k, id);
     return;
   }
-  const long long id = (long long)i + (long long)N * (j + (long long)N * k);
   const int xp = (i == N - 1) ? 1 - N : 1, xm = (i == 0) ? N - 1 : -1;
   const float* ce = e + id;
   const StencilT<float> se = gather_n<N>(ce, ce + xp, ce + xm);
   float dd = 0.f;
   if (!c.linear) {
     const float* cp = phi0 + id;
-    dd = dD32(se, gather_n<N>(cp, cp + xp, cp + xm), q0[id], c);
+    dd = dD32(se, gather_n<N>(cp, cp + xp, cp + xm), q0v, c);
   }
-  e[id] = gs_value32(se, dd, g[id], mu, c);
+  e[id] = gs_value32(se, dd, gv, mu, c);
 }
 
 __device__ __forceinline__ void b_smooth_colour32(int n, float* __restrict__ e,

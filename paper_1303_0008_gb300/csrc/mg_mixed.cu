@@ -42,9 +42,10 @@ namespace mg {
 __global__ void __launch_bounds__(256) k_residual_handoff64(
     int n, const double* __restrict__ phi, const double* __restrict__ src, OpConst64 c,
     const LevelScalars* __restrict__ sc, float* __restrict__ g, float* __restrict__ q0,
-    float* __restrict__ phi0, float* __restrict__ e, Partial* __restrict__ partials) {
+    float* __restrict__ phi0, float* __restrict__ e, Partial* __restrict__ partials,
+    float* __restrict__ gc, float* __restrict__ q0c) {
   PdlScope pdl_scope;
-  b_residual_handoff64(n, phi, src, c, sc, g, q0, phi0, e, partials, blockIdx.x);
+  b_residual_handoff64(n, phi, src, c, sc, g, q0, phi0, e, partials, blockIdx.x, gc, q0c);
 }
 
 // phi += e (FP64).
@@ -85,7 +86,9 @@ __global__ void __launch_bounds__(256) k_smooth_colour32(int n, float* __restric
 
 // The same colour stage for a power-of-two side N >= 64 known at compile time
 // (immediate neighbour offsets; cell_smooth32_n).
-template <int N>
+// CO: q0 and g in colour order (the finest level, where the hand-off writes them
+// so), the pointers already at this colour's block.
+template <int N, bool CO>
 __global__ void __launch_bounds__(256) k_smooth_colour32_n(float* __restrict__ e,
                                                            const float* __restrict__ phi0,
                                                            const float* __restrict__ q0,
@@ -96,8 +99,8 @@ __global__ void __launch_bounds__(256) k_smooth_colour32_n(float* __restrict__ e
   __shared__ float s_mu;
   if (threadIdx.x == 0) s_mu = (float)sc->lambda;
   __syncthreads();
-  cell_smooth32_n<N>(e, phi0, q0, g, s_mu, c, colour,
-                     (long long)blockIdx.x * blockDim.x + threadIdx.x);
+  cell_smooth32_n<N, CO>(e, phi0, q0, g, s_mu, c, colour,
+                         (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // The same colour stage with two cells of a row per thread (n % 4 == 0).
@@ -207,7 +210,9 @@ void mixed_release(Domain* d) {
     cudaFree(L.rhs);
     cudaFree(L.src32);
     cudaFree(L.e2);
-    L.e = L.ehat = L.phi0 = L.q0 = L.rhs = L.src32 = L.e2 = nullptr;
+    cudaFree(L.q0c);
+    cudaFree(L.rhsc);
+    L.e = L.ehat = L.phi0 = L.q0 = L.rhs = L.src32 = L.e2 = L.q0c = L.rhsc = nullptr;
   }
   cudaFree(d->d_flags);
   if (d->h_flags) cudaFreeHost(d->h_flags);
@@ -227,6 +232,10 @@ static mg_status mixed_prepare(Domain* d) {
     ok = ok && cudaMalloc(&L.rhs, b) == cudaSuccess;
     if (l > 0) ok = ok && cudaMalloc(&L.ehat, b) == cudaSuccess;
     if (sweep32_eligible(L.n)) ok = ok && cudaMalloc(&L.e2, b) == cudaSuccess;
+    if (l == 0 && L.n >= 64 && L.n <= 1024 && (L.n & (L.n - 1)) == 0) {
+      ok = ok && cudaMalloc(&L.q0c, b) == cudaSuccess;
+      ok = ok && cudaMalloc(&L.rhsc, b) == cudaSuccess;
+    }
   }
   ok = ok && cudaMalloc(&d->d_flags, 4 * sizeof(int)) == cudaSuccess;
   ok = ok && cudaMallocHost(&d->h_flags, 4 * sizeof(int)) == cudaSuccess;
@@ -304,6 +313,8 @@ struct CycleMixed {
     }
     const long long per = (long long)(L.n / 2) * (L.n / 2) * L.n;
     EventPairs* t = (l == 0 && timer && timer->enabled) ? timer : nullptr;
+    // the finest level reads q0 and g in colour order (written so by the hand-off)
+    const bool co = L.q0c != nullptr;
     for (int s = 0; s < sweeps; ++s)
       for (int colour = 0; colour < 4; ++colour) {
         const unsigned nb = nblk(per, 256);
@@ -311,26 +322,26 @@ struct CycleMixed {
         // sampled mode brackets one colour stage per call
         const bool timed = t && (!t->first_only || (s == 0 && colour == 0));
         if (timed) t->begin(st);
+        const float* qv = co ? L.q0c + colour * per : L.q0;
+        const float* gv = co ? L.rhsc + colour * per : L.rhs;
+        auto stage = [&](auto kern) {
+          launch_k(kern, nb, 256, 0, st, L.e, L.phi0, qv, gv, sc32(l), ops32[l], colour);
+        };
         switch (L.n) {
           case 64:
-            launch_k(k_smooth_colour32_n<64>, nb, 256, 0, st, L.e, L.phi0, L.q0, L.rhs, sc32(l),
-                     ops32[l], colour);
+            co ? stage(k_smooth_colour32_n<64, true>) : stage(k_smooth_colour32_n<64, false>);
             break;
           case 128:
-            launch_k(k_smooth_colour32_n<128>, nb, 256, 0, st, L.e, L.phi0, L.q0, L.rhs, sc32(l),
-                     ops32[l], colour);
+            co ? stage(k_smooth_colour32_n<128, true>) : stage(k_smooth_colour32_n<128, false>);
             break;
           case 256:
-            launch_k(k_smooth_colour32_n<256>, nb, 256, 0, st, L.e, L.phi0, L.q0, L.rhs, sc32(l),
-                     ops32[l], colour);
+            co ? stage(k_smooth_colour32_n<256, true>) : stage(k_smooth_colour32_n<256, false>);
             break;
           case 512:
-            launch_k(k_smooth_colour32_n<512>, nb, 256, 0, st, L.e, L.phi0, L.q0, L.rhs, sc32(l),
-                     ops32[l], colour);
+            co ? stage(k_smooth_colour32_n<512, true>) : stage(k_smooth_colour32_n<512, false>);
             break;
           case 1024:
-            launch_k(k_smooth_colour32_n<1024>, nb, 256, 0, st, L.e, L.phi0, L.q0, L.rhs, sc32(l),
-                     ops32[l], colour);
+            co ? stage(k_smooth_colour32_n<1024, true>) : stage(k_smooth_colour32_n<1024, false>);
             break;
           default:
             launch_k(k_smooth_colour32, nb, 256, 0, st, L.n, L.e, L.phi0, L.q0, L.rhs, sc32(l),
@@ -401,7 +412,7 @@ struct CycleMixed {
     Level& L = d->lv[0];
     const unsigned nb = nblk(L.cells, 256 * kHandoffCells);
     launch_k(k_residual_handoff64, nb, 256, 0, st, L.n, L.phi, L.src, ops[0], d->d_sc, L.rhs, L.q0,
-                                              L.phi0, L.e, d->d_part);
+             L.phi0, L.e, d->d_part, L.rhsc, L.q0c);
     count_launches(1);
     launch_finalize(st, d->d_part, (int)nb, (double)L.cells, 1, d->d_sc);
     cudaMemcpyAsync(d->h_sc, d->d_sc, sizeof(LevelScalars), cudaMemcpyDeviceToHost, st);

@@ -68,43 +68,48 @@ __device__ __forceinline__ float gal_fetch(const float* __restrict__ a, const in
 // so dA2/dSx = a1 + a2, dA2/dSy = a2 - 2 a1, dA2/dSz = a1 - 2 a2, dB/dCxy = 2 Cxy,
 // and dD/dq = sigma k2 / (2 sqrt q) (0 where the discriminant is clamped).  In
 // the conjugate form (OP_CONJ) u = src + c1h A2 + c2 B and dD/du = 1/sqrt(q).
-struct JacRow {
-  double fx, fy, fz;     // coefficient of each x, y, z face neighbour
-  double exy, exz, eyz;  // coefficient of the (+,+) and (-,-) edge neighbours; (+,-) and (-,+) take minus it
+// Each coefficient is that of the (+,+) and (-,-) neighbours of a cross
+// difference; the (+,-) and (-,+) neighbours take minus it.
+// Evaluated in FP32 on an FP32 copy of the tile: the Galerkin operator only shapes
+// the coarse-grid correction, so single precision suffices, and GB300's FP32 rate
+// is many times its FP64 rate.
+struct JacRow32 {
+  float fx, fy, fz, exy, exz, eyz;
 };
 
-__device__ __forceinline__ JacRow jac_row(const StencilT<double>& s, double src,
-                                          const OpConst64& c) {
-  JacRow r;
-  r.fx = r.fy = r.fz = c.inv_h2;
-  r.exy = r.exz = r.eyz = 0.0;
+__device__ __forceinline__ JacRow32 jac_row32(const StencilT<float>& s, float src,
+                                              const OpConst64& c) {
+  JacRow32 r;
+  const float inv_h2 = (float)c.inv_h2;
+  r.fx = r.fy = r.fz = inv_h2;
+  r.exy = r.exz = r.eyz = 0.f;
   if (c.mode == OP_LINEAR) return r;
-  const double a1 = s.sx - s.sy, a2 = s.sx - s.sz;
-  const double A2 = fma(a1, a1 - a2, a2 * a2);
-  const double Bq = fma(s.cxy, s.cxy, fma(s.cxz, s.cxz, s.cyz * s.cyz));
-  double kA = 0.0, kB = 0.0;
+  const float a1 = s.sx - s.sy, a2 = s.sx - s.sz;
+  const float A2 = fmaf(a1, a1 - a2, a2 * a2);
+  const float Bq = fmaf(s.cxy, s.cxy, fmaf(s.cxz, s.cxz, s.cyz * s.cyz));
+  float kA = 0.f, kB = 0.f;
   if (c.mode == OP_SQRT) {
-    const double q = fma(c.e1h, A2, fma(c.e2, Bq, src));
-    if (q > 0.0) {
-      const double dq = 0.5 * c.k2s * rsqrt(q);
-      kA = dq * c.e1h;
-      kB = dq * c.e2;
+    const float q = fmaf((float)c.e1h, A2, fmaf((float)c.e2, Bq, src));
+    if (q > 0.f) {
+      const float dq = 0.5f * (float)c.k2s * rsqrtf(q);
+      kA = dq * (float)c.e1h;
+      kB = dq * (float)c.e2;
     }
   } else {
-    const double u = fma(c.c1h, A2, fma(c.c2, Bq, src));
-    const double q = fma(c.c3, u, 1.0);
-    if (q > 0.0) {
-      const double du = rsqrt(q);
-      kA = du * c.c1h;
-      kB = du * c.c2;
+    const float u = fmaf((float)c.c1h, A2, fmaf((float)c.c2, Bq, src));
+    const float q = fmaf((float)c.c3, u, 1.f);
+    if (q > 0.f) {
+      const float du = rsqrtf(q);
+      kA = du * (float)c.c1h;
+      kB = du * (float)c.c2;
     }
   }
-  r.fx = fma(-kA, a1 + a2, c.inv_h2);
-  r.fy = fma(-kA, a2 - 2.0 * a1, c.inv_h2);
-  r.fz = fma(-kA, a1 - 2.0 * a2, c.inv_h2);
-  r.exy = -2.0 * kB * s.cxy;
-  r.exz = -2.0 * kB * s.cxz;
-  r.eyz = -2.0 * kB * s.cyz;
+  r.fx = fmaf(-kA, a1 + a2, inv_h2);
+  r.fy = fmaf(-kA, a2 - 2.f * a1, inv_h2);
+  r.fz = fmaf(-kA, a1 - 2.f * a2, inv_h2);
+  r.exy = -2.f * kB * s.cxy;
+  r.exz = -2.f * kB * s.cxz;
+  r.eyz = -2.f * kB * s.cyz;
   return r;
 }
 
@@ -119,18 +124,18 @@ __host__ __device__ constexpr int s19(int e, int axis) {
   return tab[e][axis];
 }
 
-__device__ __forceinline__ float row_entry(const JacRow& r, double centre, int s) {
+__device__ __forceinline__ float row_entry(const JacRow32& r, float centre, int s) {
   switch (s) {
-    case 0: return (float)centre;
-    case 1: case 2: return (float)r.fx;
-    case 3: case 4: return (float)r.fy;
-    case 5: case 6: return (float)r.fz;
-    case 7: case 8: return (float)r.exy;
-    case 9: case 10: return (float)(-r.exy);
-    case 11: case 12: return (float)r.exz;
-    case 13: case 14: return (float)(-r.exz);
-    case 15: case 16: return (float)r.eyz;
-    default: return (float)(-r.eyz);
+    case 0: return centre;
+    case 1: case 2: return r.fx;
+    case 3: case 4: return r.fy;
+    case 5: case 6: return r.fz;
+    case 7: case 8: return r.exy;
+    case 9: case 10: return -r.exy;
+    case 11: case 12: return r.exz;
+    case 13: case 14: return -r.exz;
+    case 15: case 16: return r.eyz;
+    default: return -r.eyz;
   }
 }
 
@@ -154,6 +159,20 @@ __device__ __forceinline__ void gal_scatter(float (&acc)[27], unsigned cmask, fl
     const int o = (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
     if ((cmask >> o) & 1u) acc[o] = fmaf(w, v, acc[o]);
   }
+}
+
+// Face sums and cross differences of cell (i,j,k) of an FP32 copy of a ghosted
+// 10^3 patch tile.
+__device__ __forceinline__ StencilT<float> gather_tile32(const float* t, int i, int j, int k) {
+  auto at = [&](int a, int b, int cc) { return t[(a + 1) + 10 * ((b + 1) + 10 * (cc + 1))]; };
+  StencilT<float> s;
+  s.sx = at(i + 1, j, k) + at(i - 1, j, k);
+  s.sy = at(i, j + 1, k) + at(i, j - 1, k);
+  s.sz = at(i, j, k + 1) + at(i, j, k - 1);
+  s.cxy = (at(i + 1, j + 1, k) + at(i - 1, j - 1, k)) - (at(i + 1, j - 1, k) + at(i - 1, j + 1, k));
+  s.cxz = (at(i + 1, j, k + 1) + at(i - 1, j, k - 1)) - (at(i + 1, j, k - 1) + at(i - 1, j, k + 1));
+  s.cyz = (at(i, j + 1, k + 1) + at(i, j - 1, k - 1)) - (at(i, j + 1, k - 1) + at(i, j - 1, k + 1));
+  return s;
 }
 
 // Bit r of the result is set when neighbour block r (0..26, the patch table's
@@ -190,9 +209,12 @@ __global__ void __launch_bounds__(64) k_gal_assemble0(const double* __restrict__
                                                       const int* __restrict__ nbr, OpConst64 c,
                                                       float* __restrict__ J1) {
   __shared__ double tile[1000];
+  __shared__ float tile32[1000];
   const int p = blockIdx.x;
   load_tile<8>(tile, p, phi, ghost, nbr);
   const unsigned exm = exist_mask(nbr, p);
+  __syncthreads();
+  for (int q = threadIdx.x; q < 1000; q += blockDim.x) tile32[q] = (float)tile[q];
   __syncthreads();
   const int t = threadIdx.x;
   const int I = t & 3, J = (t >> 2) & 3, K = t >> 4;
@@ -200,13 +222,13 @@ __global__ void __launch_bounds__(64) k_gal_assemble0(const double* __restrict__
   float acc[27];
 #pragma unroll
   for (int o = 0; o < 27; ++o) acc[o] = 0.0f;
-  const double centre = -6.0 * c.inv_h2;
+  const float centre = (float)(-6.0 * c.inv_h2);
 #pragma unroll
   for (int ch = 0; ch < 8; ++ch) {
     const int cx = ch & 1, cy = (ch >> 1) & 1, cz = ch >> 2;
     const int x = 2 * I + cx, y = 2 * J + cy, z = 2 * K + cz;
-    const StencilT<double> s = gather_tile<8>(tile, x, y, z);
-    const JacRow r = jac_row(s, src[(long long)p * 512 + x + 8 * (y + 8 * z)], c);
+    const StencilT<float> s = gather_tile32(tile32, x, y, z);
+    const JacRow32 r = jac_row32(s, (float)src[(long long)p * 512 + x + 8 * (y + 8 * z)], c);
 #pragma unroll
     for (int e = 0; e < 19; ++e) {
       const int sx = s19(e, 0), sy = s19(e, 1), sz = s19(e, 2);

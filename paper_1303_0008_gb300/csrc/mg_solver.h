@@ -28,6 +28,8 @@ struct Level {
   float* rhs = nullptr;      // right-hand side of N(e) = rhs (+ mu)
   float* src32 = nullptr;    // kappa * delta in FP32 (coarse levels)
   float* e2 = nullptr;       // second correction buffer of the one-launch sweep
+  float* q0c = nullptr;      // finest level: q0 and rhs again, in colour order, for the
+  float* rhsc = nullptr;     // colour stages (contiguous reads of a colour's own cells)
 };
 
 struct Domain {

@@ -89,6 +89,39 @@ def test_c4_512_mixed_and_fp64():
     assert rel(O.force(out[1][1]), O.force(out[0][1])) < 1e-7
 
 
+def test_c4_512_against_one_oracle_solve():
+    """C4 at full size against one oracle solve of the same system: the oracle's
+    four-colour OpenMP build (pinned to the lexicographic oracle's fixed point)
+    solves the floored 512^3 system to 1e-10 on the host cores; the GPU's FP64
+    solve to the same residual and its mixed-precision solve to 1e-8 are compared
+    with it element by element, for phi and for the force -grad(phi)/2."""
+    n = 512
+    delta = I.lognormal_delta(n, 2.0, 1304)
+    alpha = I.alpha_kappa_for_rv(16.0)
+    fl, _ = O.density_floor(delta, alpha, 1.0)
+    ref, rst = O.fas_solve_colour(fl, alpha, 1.0, tol=1e-10, max_cycles=100)
+    assert rst["status"] == O.OK, rst
+    ref_force = O.force(ref)
+    # two solutions of the same system with residuals below 1e-10 differ by about
+    # res / (4 pi^2) = 3e-12 absolute, i.e. 1e-9 of max|phi| (~3e-3); the mixed solve
+    # stops at 1e-8, and its bound is the 1e-7 of the precision target
+    for prec, tol, bound in ((0, 1e-10, 2e-9), (1, TOL, 1e-7)):
+        g = mg.mg_create_grid(n, mg.options(prec=prec))
+        try:
+            mg.mg_set_density(g, 0, -1, torch.from_numpy(delta).cuda())
+            st = mg.mg_solve(g, 0, alpha, 1.0, tol)
+            phi = torch.empty((n, n, n), dtype=torch.float64, device="cuda")
+            mg.mg_get_field(g, 0, -1, phi)
+            force = torch.empty((3, n, n, n), dtype=torch.float64, device="cuda")
+            mg.mg_get_force(g, 0, -1, force)
+        finally:
+            mg.mg_destroy_grid(g)
+        assert st["rc"] == mg.MG_OK
+        assert rel(phi.cpu().numpy(), ref) < bound, prec
+        assert rel(force.cpu().numpy(), ref_force) < bound, prec
+        del phi, force
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_largest_grid_1024_sampled_residual(prec):
     """n = 1024, the largest grid the library accepts (2^30 cells per array):
