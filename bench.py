@@ -180,6 +180,10 @@ _KERNEL_SOURCES = {
     "k_smooth_colour32_n": (("mg_bodies32.cuh", "mg_common.cuh"), "mg_mixed.cu",
                             ("__global__ void __launch_bounds__(256) k_smooth_colour32_n(",
                              "  void smooth(int l, int sweeps) const {")),
+    "k_smooth_slab32": (("mg_bodies32.cuh", "mg_common.cuh"), "mg_mixed.cu",
+                        ("__global__ void __launch_bounds__(256) k_smooth_slab32(",
+                         "  void slab_sweeps(int l, int sweeps, bool co, EventPairs* t) const {"),
+                        (("mg_internal.h", "inline void slab_range("),)),
 }
 
 
@@ -187,14 +191,14 @@ def kernel_source_hash(kernel: str = "k_smooth_colour64"):
     """Hash of the source that defines `kernel` and its launch: the headers its body
     comes from, plus the kernel and its launcher in its translation unit (other
     kernels in that file do not change it)."""
-    headers, unit, heads = _KERNEL_SOURCES[kernel]
+    headers, unit, heads, *more = _KERNEL_SOURCES[kernel]
     csrc = os.path.join(ROOT, "paper_1303_0008_gb300", "csrc")
     h = hashlib.sha256()
     for f in headers:
         h.update(open(os.path.join(csrc, f), "rb").read())
-    text = open(os.path.join(csrc, unit)).read()
-    for head in heads:
-        part = _definition(text, head)
+    parts = [(unit, head) for head in heads] + list(more[0] if more else ())
+    for f, head in parts:
+        part = _definition(open(os.path.join(csrc, f)).read(), head)
         assert part, head
         h.update(part.encode())
     return h.hexdigest()[:16]
@@ -292,7 +296,7 @@ def run_ours(args):
                                      use_cache=False)
         tuned["fp64" if prec == mg.MG_FP64 else "mixed"] = {
             "nu_pre": best.nu_pre, "nu_post": best.nu_post, "inner_cycles": best.inner_cycles,
-            "half32": best.half32, "tune_s": time.perf_counter() - t0}
+            "half32": best.half32, "slab32": best.slab32, "tune_s": time.perf_counter() - t0}
         return g, best
 
     g64, best64 = tune(mg.MG_FP64)
@@ -323,10 +327,12 @@ def run_ours(args):
     if not hbm_peak:
         hbm_peak, peak_src = HBM_FALLBACK_GBS, "fallback 6.8 TB/s"
     # FP32 correction smoother, HBM-bound: algorithmic bytes per launch / event time;
-    # a timed launch is one colour stage, or one half sweep (two colours)
+    # a timed unit is one colour stage, one half sweep (two colours), or one whole
+    # sweep of slab launches
     avg32, cells32, n32 = kernel_rate(stats_m)
     ach32 = BYTES_PER_CELL_FP32 * cells32 / avg32 / 1e9
-    k32 = "k_half32" if bestmx.half32 else "k_smooth_colour32_n"
+    slab = bestmx.slab32 if (not bestmx.half32 and N >= 256 and N % max(bestmx.slab32, 1) == 0) else 0
+    k32 = "k_half32" if bestmx.half32 else "k_smooth_slab32" if slab else "k_smooth_colour32_n"
     traffic32 = traffic_per_launch(k32, cells32)
     # FP64 smoother, bound by the FP64 pipe
     avg64, cells64, n64 = kernel_rate(stats)
@@ -335,6 +341,8 @@ def run_ours(args):
     roofline = {
         "bound": "hbm",
         "kernel": (f"k_half32<{N}> (finest FP32 half sweep, two colours, mixed)" if bestmx.half32
+                   else f"k_smooth_slab32<{N}> (finest FP32 sweep in slabs of {slab} planes, "
+                        f"{4 * N // max(slab, 1)} launches; one timed unit is a whole sweep)" if slab
                    else f"k_smooth_colour32_n<{N}> (finest FP32 colour stage, mixed)"),
         "achieved": ach32, "peak": hbm_peak, "unit": "GB/s", "frac": ach32 / hbm_peak,
         "traffic": traffic32, "peak_source": peak_src,
@@ -386,19 +394,21 @@ def run_ours(args):
         e2e_step()
     barrier()
     e2e_ms = []
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e2e_step()
-        torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    with ClockSampler(local) as clk_e2e:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
     barrier()
     mg.mg_destroy_grid(ge)
     e2e_total = max_over_ranks(sum(e2e_ms))
     cell_bytes = delta_np.size * 8
     e2e = {"value": solves_done / (e2e_total * 1e-3), "unit": "solves/s",
-           "h2d_bytes_per_step": 2 * cell_bytes, "d2h_bytes_per_step": cell_bytes}
+           "h2d_bytes_per_step": 2 * cell_bytes, "d2h_bytes_per_step": cell_bytes,
+           "ms_per_step": e2e_total / args.steps, "clocks": clk_e2e.summary()}
 
     s0, m0 = stats[0], stats_m[0]
     line = {

@@ -100,8 +100,9 @@ typedef struct {
                         first colour stage of each smoothing call only (an event
                         between two launches removes their programmatic overlap, so
                         this disturbs the solve less); default 0.  With MG_MIXED the
-                        timed launches are the finest level's FP32 colour stages (not
-                        timed with sweep32 or pair32). */
+                        timed launches are the finest level's FP32 colour stages (a half
+                        sweep with half32; a whole sweep of slab launches with slab32;
+                        not timed with sweep32 or pair32). */
   mg_guard guard;    /* default MG_GUARD_FLOOR */
   int patch_coarse_sweeps; /* sweeps on the coarsest (2^3 per patch) level of a
                               refinement union per V-cycle (default 8) */
@@ -147,6 +148,13 @@ typedef struct {
   double barrier_timeout_s; /* longest wait of a kernel for its asynchronous copies
                         (default 1 s); a kernel that waits longer records the failure
                         and returns, and the solve returns MG_ETIMEOUT */
+  int slab32;        /* mixed precision, levels with n >= 256 (a power of two) and
+                        n % slab32 == 0: > 0 runs each FP32 correction sweep slab by slab,
+                        slab32 z planes per launch and colour, each colour a few planes
+                        behind the one before it, so that a colour stage finds the planes
+                        it reads in L2 (same arithmetic, same bits as whole colour
+                        stages); one of 0 (whole colour stages, default), 8, 16, 32, 64,
+                        128, 256. */
 } mg_options;
 
 typedef struct {
@@ -251,10 +259,12 @@ mg_status mg_set_options(mg_grid* g, const mg_options* opt);
 /*
  * Autotuner.  Solves the handle's problem (its density and the field the caller
  * left in it, restored before every trial) with every combination of a sweep
- * pair (nu_pre, nu_post) from {1,1 2,1 1,2 2,2 3,2 2,3 3,3 4,3 3,4 4,4}, for
- * MG_MIXED inner_cycles in {3,4} and (n = 256 or 512) half32 in {0,1}, and
- * for n <= 64 fuse_coarse in {0,1}; each candidate is solved and timed on the
- * device (twice for n <= 64, where the second solve counts).  The fastest
+ * pair (nu_pre, nu_post) from {1,1 2,1 1,2 2,2 3,2 2,3 3,3 4,3 3,4 4,4 5,4 4,5
+ * 5,5}, for MG_MIXED inner_cycles in {3,4}, and for n <= 64 fuse_coarse in
+ * {0,1}.  For MG_MIXED with n >= 256 it then tries, at the winning counts, the
+ * shapes of the FP32 sweep: whole colour stages, slabs of slab32 in {8,16,32,64}
+ * planes, and (n = 256 or 512) half32 = 1.  Each candidate is solved and timed
+ * on the device (twice for n <= 64, where the second solve counts).  The fastest
  * candidate that converges to
  * `tol` becomes the handle's options and is returned in *best (may be NULL) with
  * its time in *best_seconds (may be NULL).  With a cache_path, the choice is
@@ -267,6 +277,21 @@ mg_status mg_set_options(mg_grid* g, const mg_options* opt);
 mg_status mg_autotune(mg_grid* g, int branch, double alpha, double kappa, double tol,
                       const char* cache_path, int use_cache, mg_options* best,
                       double* best_seconds);
+
+/*
+ * The launch order of one FP32 correction sweep in slabs (option slab32; host
+ * only, no GPU needed): launch m updates the cells of colour colour[m]
+ * (c = ((i+k)&1) + 2((j+k)&1)) on the planes z0[m], ..., z0[m] + nz[m] - 1 (mod n).
+ * The n/slab slabs run in order and, within a slab, colours 0 to 3; colour c's
+ * slabs sit c planes below colour 0's, and its first c planes come in its last
+ * slab.  Every cell then reads the same neighbour values as in four whole colour
+ * stages (Sec. III.B's Gauss-Seidel order), and each launch reads planes that the
+ * launch before it touched.  Writes 4 n/slab entries into each array (cap entries
+ * at most) and their number into *count.
+ * Errors: MG_EINVAL (no slab order for this n and slab: slab < 8, n % slab != 0,
+ * n / slab < 2, or cap too small; a NULL pointer).
+ */
+mg_status mg_slab_order(int n, int slab, int* colour, int* z0, int* nz, int cap, int* count);
 
 /* Statistics of the last solve of a refinement level (level >= 1): cycles,
  * status, final residual, the residual after each cycle and the device time of

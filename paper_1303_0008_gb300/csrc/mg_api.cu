@@ -54,6 +54,7 @@ void mg_default_options(mg_options* opt) {
   opt->patch_galerkin = 1;
   opt->half32 = 0;
   opt->barrier_timeout_s = 1.0;
+  opt->slab32 = 0;
 }
 
 static mg_status check_options(const mg_options& o) {
@@ -83,6 +84,8 @@ static mg_status check_options(const mg_options& o) {
   if (o.half32 != 0 && o.half32 != 1) MG_FAIL(MG_EINVAL, "options: half32");
   if (!(o.barrier_timeout_s >= 0.0 && o.barrier_timeout_s <= 3600.0))
     MG_FAIL(MG_EINVAL, "options: barrier_timeout_s must be in [0, 3600]");
+  if (o.slab32 != 0 && !(o.slab32 >= 8 && o.slab32 <= 256 && (o.slab32 & (o.slab32 - 1)) == 0))
+    MG_FAIL(MG_EINVAL, "options: slab32 must be 0 or a power of two from 8 to 256");
   return MG_OK;
 }
 
@@ -641,6 +644,22 @@ mg_status mg_get_total_force(const mg_grid* g_const, int level, int patch, doubl
   const mg_status st = mg_get_force(g, level, patch, out, on_device);
   swap_fields(g, g->nw_psi, g->nw_psi_ghost);
   return st;
+}
+
+mg_status mg_slab_order(int n, int slab, int* colour, int* z0, int* nz, int cap, int* count) {
+  if (!colour || !z0 || !nz || !count) MG_FAIL(MG_EINVAL, "mg_slab_order: NULL pointer");
+  if (n < 16 || n > 1024 || slab < 8 || n % slab != 0 || n / slab < 2)
+    MG_FAIL(MG_EINVAL, "mg_slab_order: needs slab >= 8, n % slab == 0 and n / slab >= 2");
+  const int total = 4 * (n / slab);
+  if (cap < total) MG_FAIL(MG_EINVAL, "mg_slab_order: cap smaller than 4 n / slab");
+  int m = 0;
+  for (int s = 0; s < n / slab; ++s)
+    for (int c = 0; c < 4; ++c, ++m) {
+      colour[m] = c;
+      slab_range(n, slab, c, s, &z0[m], &nz[m]);
+    }
+  *count = total;
+  return MG_OK;
 }
 
 }  // extern "C"

@@ -1,6 +1,7 @@
 // Autotuner: pick the sweep counts (and, for the mixed path, the inner V-cycles
-// per FP64 correction and the shape of the FP32 sweep: four colour launches or
-// two half sweeps over tiles of whole rows) that give the shortest time to the
+// per FP64 correction and the shape of the FP32 sweep: four colour launches, slabs
+// of z planes in a staggered order, or two half sweeps over tiles of whole rows)
+// that give the shortest time to the
 // requested residual on the handle's own problem, and remember the choice in a
 // small JSON file keyed by grid size, precision and device name.
 //
@@ -125,6 +126,7 @@ extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double ka
     o.inner_cycles = (int)e.at("inner_cycles");
     o.fuse_coarse = (int)e.at("fuse_coarse");
     if (e.count("half32")) o.half32 = (int)e.at("half32");
+    if (e.count("slab32")) o.slab32 = (int)e.at("slab32");
     g->opt = o;
     if (best) *best = o;
     if (best_seconds) *best_seconds = e.count("seconds") ? e.at("seconds") : -1.0;
@@ -139,37 +141,35 @@ extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double ka
   }
   cudaMemcpyAsync(saved, d->lv[0].phi, bytes, cudaMemcpyDeviceToDevice, g->stream);
   const mg_options base = g->opt;
-  // Candidates: pre/post sweep pairs up to 4 that differ by at most one (the
+  // First stage: pre/post sweep pairs up to 5 that differ by at most one (the
   // strongly nonlinear workloads want more smoothing than the 2/2 default); for
-  // the mixed path 3 or 4 inner V-cycles per FP64 correction and, where the
-  // grid supports it, the FP32 sweep as four colour launches or two half sweeps;
-  // the coarse-level fusion only where it matters (n <= 64).
-  std::vector<mg_options> cands;
-  const int pairs[][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 2}, {2, 3},
-                          {3, 3}, {4, 3}, {3, 4}, {4, 4}};
+  // the mixed path 3 or 4 inner V-cycles per FP64 correction; the coarse-level
+  // fusion only where it matters (n <= 64).  The FP32 sweep shapes give the same
+  // bits, so they change the cost of a sweep and not the cycle count: the second
+  // stage tries them at the first stage's counts only.
+  const int pairs[][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 2}, {2, 3}, {3, 3},
+                          {4, 3}, {3, 4}, {4, 4}, {5, 4}, {4, 5}, {5, 5}};
   const bool mixed = base.prec == MG_MIXED;
   const int inner_set[] = {3, 4};
-  const bool half_ok = mixed && half_sweep_supported(d->n);
   const bool fuse_matters = d->n <= 64;
+  std::vector<mg_options> cands;
   for (const auto& pp : pairs)
     for (int ic = 0; ic < (mixed ? 2 : 1); ++ic)
-      for (int half = 0; half <= (half_ok ? 1 : 0); ++half)
-        for (int fuse = 0; fuse <= (fuse_matters ? 1 : 0); ++fuse) {
-          mg_options o = base;
-          o.nu_pre = pp[0];
-          o.nu_post = pp[1];
-          o.inner_cycles = mixed ? inner_set[ic] : base.inner_cycles;
-          o.half32 = half_ok ? half : base.half32;
-          o.fuse_coarse = fuse_matters ? fuse : base.fuse_coarse;
-          cands.push_back(o);
-        }
+      for (int fuse = 0; fuse <= (fuse_matters ? 1 : 0); ++fuse) {
+        mg_options o = base;
+        o.nu_pre = pp[0];
+        o.nu_post = pp[1];
+        o.inner_cycles = mixed ? inner_set[ic] : base.inner_cycles;
+        o.fuse_coarse = fuse_matters ? fuse : base.fuse_coarse;
+        cands.push_back(o);
+      }
   // small grids: two solves per candidate (the first also captures the graphs and
   // is noisier); from 128^3 on a solve is long enough to time once
   const int reps = d->n <= 64 ? 2 : 1;
   double t_best = 1e300;
   mg_options o_best = base;
   mg_status result = MG_ENOCONV;
-  for (const mg_options& o : cands) {
+  auto trial = [&](const mg_options& o) {
     double t = 0.0;
     bool ok = true;
     for (int rep = 0; rep < reps && ok; ++rep) {
@@ -184,6 +184,32 @@ extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double ka
       o_best = o;
       result = MG_OK;
     }
+  };
+  for (const mg_options& o : cands) trial(o);
+  // Second stage (mixed, n >= 256): whole colour stages, slabs, half sweeps.
+  if (mixed && result == MG_OK && d->n >= 256) {
+    const mg_options first = o_best;
+    std::vector<mg_options> shapes;
+    mg_options o = first;
+    o.half32 = 0;
+    o.sweep32 = 0;
+    o.pair32 = 0;
+    o.slab32 = 0;
+    shapes.push_back(o);
+    for (int S : {8, 16, 32, 64})
+      if (slab_sweep_applies(d->n, S)) {
+        o.slab32 = S;
+        shapes.push_back(o);
+      }
+    if (half_sweep_supported(d->n)) {
+      o.slab32 = 0;
+      o.half32 = 1;
+      shapes.push_back(o);
+    }
+    for (const mg_options& c : shapes)
+      if (c.half32 != first.half32 || c.slab32 != first.slab32 || c.sweep32 != first.sweep32 ||
+          c.pair32 != first.pair32)
+        trial(c);
   }
   cudaMemcpyAsync(d->lv[0].phi, saved, bytes, cudaMemcpyDeviceToDevice, g->stream);
   cudaStreamSynchronize(g->stream);
@@ -201,6 +227,7 @@ extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double ka
                   {"inner_cycles", (double)o_best.inner_cycles},
                   {"fuse_coarse", (double)o_best.fuse_coarse},
                   {"half32", (double)o_best.half32},
+                  {"slab32", (double)o_best.slab32},
                   {"seconds", t_best}};
     if (!write_cache(cache_path, cache)) {
       set_error("mg_autotune: cannot write the cache file");

@@ -222,6 +222,29 @@ void launch_half_sweep32(cudaStream_t st, int n, const float* e_in, float* e_out
                          const LevelScalars* sc, const OpConst32& c, int* err, double limit_s,
                          EventPairs* timer = nullptr);
 
+// Staggered slab order of one four-colour sweep (option slab32, mg_mixed.cu).
+// The n planes are cut into n / S slabs of S planes; slab s of colour c covers
+// planes [a, b) (mod n) with
+//   a = c (s = 0), S s - c (s > 0);   b = S (s + 1) - c (s < n/S - 1), n + c (last).
+// The launches run slab by slab and, within a slab, colour by colour.  A cell of
+// colour c reads only cells of the other colours, on its own plane and the two
+// beside it.  When slab s of colour c runs, colour c - 1 has updated every plane up
+// to b (its own slab s ends one plane later) and down to a - 1, and colour c + 1 has
+// updated nothing that colour c still reads (its slabs end one plane earlier);
+// colour c's first c planes wait for the last slab, after colour c - 1 has wrapped
+// around.  So every cell sees the values of the whole-stage order, and the planes a
+// launch reads were read or written by the launch before it.
+inline bool slab_sweep_applies(int n, int S) {
+  return S >= 8 && n >= 256 && (n & (n - 1)) == 0 && n % S == 0 && n / S >= 2;
+}
+inline void slab_range(int n, int S, int colour, int s, int* z0, int* nz) {
+  const int ns = n / S;
+  const int a = s == 0 ? colour : S * s - colour;
+  const int b = s == ns - 1 ? n + colour : S * (s + 1) - colour;
+  *z0 = a;
+  *nz = b - a;
+}
+
 // One-launch four-colour sweep of the FP32 correction operator (mg_sweep32.cu):
 // reads e_in, writes every cell of e_out; n >= 32 and n % 4 == 0.
 bool sweep32_eligible(int n);

@@ -103,6 +103,26 @@ __global__ void __launch_bounds__(256) k_smooth_colour32_n(float* __restrict__ e
                          (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// The colour stage of k_smooth_colour32_n on the planes z0, ..., z0 + nz - 1 (mod
+// N) only: one launch of a sweep run slab by slab (slab_range).
+template <int N, bool CO>
+__global__ void __launch_bounds__(256) k_smooth_slab32(float* __restrict__ e,
+                                                       const float* __restrict__ phi0,
+                                                       const float* __restrict__ q0,
+                                                       const float* __restrict__ g,
+                                                       const LevelScalars* __restrict__ sc,
+                                                       OpConst32 c, int colour, int z0, int nz) {
+  PdlScope pdl_scope;
+  __shared__ float s_mu;
+  if (threadIdx.x == 0) s_mu = (float)sc->lambda;
+  __syncthreads();
+  constexpr long long HH = (long long)(N / 2) * (N / 2);
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= HH * nz) return;
+  const int k = (z0 + (int)(t / HH)) & (N - 1);
+  cell_smooth32_n<N, CO>(e, phi0, q0, g, s_mu, c, colour, (long long)k * HH + t % HH);
+}
+
 // The same colour stage with two cells of a row per thread (n % 4 == 0).
 __global__ void __launch_bounds__(256) k_smooth_colour32_pair(int n, float* __restrict__ e,
                                                               const float* __restrict__ phi0,
@@ -315,6 +335,10 @@ struct CycleMixed {
     EventPairs* t = (l == 0 && timer && timer->enabled) ? timer : nullptr;
     // the finest level reads q0 and g in colour order (written so by the hand-off)
     const bool co = L.q0c != nullptr;
+    if (slab_sweep_applies(L.n, o->slab32)) {
+      slab_sweeps(l, sweeps, co, t);
+      return;
+    }
     for (int s = 0; s < sweeps; ++s)
       for (int colour = 0; colour < 4; ++colour) {
         const unsigned nb = nblk(per, 256);
@@ -350,6 +374,40 @@ struct CycleMixed {
         if (timed) t->end(st);
       }
     count_launches(4LL * sweeps);
+  }
+
+  // Sweeps in the staggered slab order (slab_range); a timed unit is one whole sweep.
+  void slab_sweeps(int l, int sweeps, bool co, EventPairs* t) const {
+    Level& L = d->lv[l];
+    const int S = o->slab32, ns = L.n / S;
+    const long long hh = (long long)(L.n / 2) * (L.n / 2);
+    for (int sw = 0; sw < sweeps; ++sw) {
+      const bool timed = t && (!t->first_only || sw == 0);
+      if (timed) t->begin(st);
+      for (int s = 0; s < ns; ++s)
+        for (int colour = 0; colour < 4; ++colour) {
+          int z0 = 0, nz = 0;
+          slab_range(L.n, S, colour, s, &z0, &nz);
+          const unsigned nb = nblk(hh * nz, 256);
+          const float* qv = co ? L.q0c + colour * hh * L.n : L.q0;
+          const float* gv = co ? L.rhsc + colour * hh * L.n : L.rhs;
+          auto stage = [&](auto kern) {
+            launch_k(kern, nb, 256, 0, st, L.e, L.phi0, qv, gv, sc32(l), ops32[l], colour, z0, nz);
+          };
+          switch (L.n) {
+            case 256:
+              co ? stage(k_smooth_slab32<256, true>) : stage(k_smooth_slab32<256, false>);
+              break;
+            case 512:
+              co ? stage(k_smooth_slab32<512, true>) : stage(k_smooth_slab32<512, false>);
+              break;
+            default:
+              co ? stage(k_smooth_slab32<1024, true>) : stage(k_smooth_slab32<1024, false>);
+          }
+        }
+      if (timed) t->end(st);
+    }
+    count_launches(4LL * ns * sweeps);
   }
 
   void subcycle(int l) const {
@@ -446,6 +504,7 @@ mg_status mixed_solve(Domain* d, const mg_options& o, cudaStream_t st, const OpC
   // the finest FP32 colour stages are timed when they run as per-colour launches
   EventPairs tb;
   const bool half = o.half32 && half_sweep_supported(d->lv[0].n);
+  const bool slab = !half && !o.sweep32 && !o.pair32 && slab_sweep_applies(d->lv[0].n, o.slab32);
   tb.enabled = o.time_kernels != 0 && (half || (!o.sweep32 && !o.pair32));
   tb.first_only = o.time_kernels == 2;
   MCK(cudaMemsetAsync(d->d_flags, 0, sizeof(int), st));
@@ -460,8 +519,8 @@ mg_status mixed_solve(Domain* d, const mg_options& o, cudaStream_t st, const OpC
   }
   const bool graphs = o.use_graphs && d->gexec[2] && d->gexec[3];
   const int pairs_b = tb.n;
-  // a timed launch is one colour stage, or with half sweeps one half sweep
-  const double cells_per_launch = (double)d->lv[0].cells / (half ? 2.0 : 4.0);
+  // a timed unit is one colour stage, one half sweep, or one whole sweep of slabs
+  const double cells_per_launch = (double)d->lv[0].cells / (half ? 2.0 : slab ? 1.0 : 4.0);
   bool b_pending = false;
   auto harvest = [&]() {
     if (!tb.enabled || !b_pending) return;

@@ -321,6 +321,8 @@ __global__ void __launch_bounds__(64) k_gal_smooth(const float* __restrict__ J,
   const int k = 2 * (u / (H * H)) + (colour >> 2);
   const int t = i + B * (j + B * k);
   const float diag = J[((long long)p * 27 + 13) * BC + t];
+  // a row whose assembled diagonal vanished (or is not finite) keeps its value
+  if (!(fabsf(diag) > 0.f) || !isfinite(diag)) return;
   const float r = b[(long long)p * BC + t] - gal_offdiag<B>(J, e, nbr, p, i, j, k);
   e[(long long)p * BC + t] = r / diag;
 }

@@ -41,7 +41,7 @@ class mg_options(ctypes.Structure):
                 ("sweep32", ctypes.c_int), ("pair32", ctypes.c_int),
                 ("tau_stop", ctypes.c_double), ("w", ctypes.c_double),
                 ("patch_galerkin", ctypes.c_int), ("half32", ctypes.c_int),
-                ("barrier_timeout_s", ctypes.c_double)]
+                ("barrier_timeout_s", ctypes.c_double), ("slab32", ctypes.c_int)]
 
 
 class mg_solve_stats(ctypes.Structure):
@@ -101,6 +101,8 @@ _SIGS = {
     "mg_get_level_stats": (_I, [_P, _I, ctypes.POINTER(mg_solve_stats)]),
     "mg_set_options": (_I, [_P, ctypes.POINTER(mg_options)]),
     "mg_autotune": (_I, [_P, _I, _F, _F, _F, ctypes.c_char_p, _I, ctypes.POINTER(mg_options), _D]),
+    "mg_slab_order": (_I, [_I, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_int), _I, ctypes.POINTER(ctypes.c_int)]),
 }
 
 
@@ -332,6 +334,16 @@ def mg_autotune(g, branch, alpha, kappa, tol, cache_path=None, use_cache=True):
     _check(lib().mg_autotune(g, branch, alpha, kappa, tol, path, int(bool(use_cache)),
                              ctypes.byref(o), ctypes.byref(t)), "mg_autotune")
     return o, t.value
+
+
+def mg_slab_order(n, slab):
+    """Launch order of one FP32 sweep in slabs: a list of (colour, z0, nz)."""
+    cap = 4 * max(n // max(slab, 1), 1)
+    arr = [(ctypes.c_int * cap)() for _ in range(3)]
+    count = ctypes.c_int()
+    _check(lib().mg_slab_order(n, slab, arr[0], arr[1], arr[2], cap, ctypes.byref(count)),
+           "mg_slab_order")
+    return [(arr[0][m], arr[1][m], arr[2][m]) for m in range(count.value)]
 
 
 def options_dict(o: mg_options) -> dict:

@@ -46,7 +46,8 @@ def test_single_process_aggregation_is_identity():
     assert bench.max_over_ranks(3.5) == 3.5 and bench.sum_over_ranks(6.0) == 6.0
 
 
-@pytest.mark.parametrize("kernel", ["k_smooth_colour64", "k_smooth_colour32_n", "k_half32"])
+@pytest.mark.parametrize("kernel", ["k_smooth_colour64", "k_smooth_colour32_n", "k_half32",
+                                    "k_smooth_slab32"])
 def test_traffic_record_matches_the_smoother_source(kernel):
     """The benchmark's DRAM-traffic figures are tied to a hash of each roofline
     kernel's source (the headers of its body, the kernel and its launcher).  The
@@ -55,10 +56,10 @@ def test_traffic_record_matches_the_smoother_source(kernel):
     import json
     import bench
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    headers, unit, heads = bench._KERNEL_SOURCES[kernel]
-    text = open(os.path.join(root, "paper_1303_0008_gb300", "csrc", unit)).read()
-    for head in heads:
-        part = bench._definition(text, head)
+    headers, unit, heads, *more = bench._KERNEL_SOURCES[kernel]
+    csrc = os.path.join(root, "paper_1303_0008_gb300", "csrc")
+    for f, head in [(unit, h) for h in heads] + list(more[0] if more else ()):
+        part = bench._definition(open(os.path.join(csrc, f)).read(), head)
         assert part.startswith(head) and part.rstrip().endswith("}")
     rec = json.load(open(os.path.join(root, "profiles", "traffic.json")))[kernel]
     assert rec["source_hash"] == bench.kernel_source_hash(kernel)

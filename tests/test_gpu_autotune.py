@@ -30,7 +30,7 @@ def test_autotune_picks_caches_and_restores(tmp_path, prec):
         phi0 = 1e-3 * I.random_field(n, 3)
         mg.mg_set_field(g, 0, -1, phi0)
         best, t = mg.mg_autotune(g, 0, a, 1.0, 1e-10, cache, use_cache=False)
-        assert t > 0 and 1 <= best.nu_pre <= 4 and 1 <= best.nu_post <= 4
+        assert t > 0 and 1 <= best.nu_pre <= 5 and 1 <= best.nu_post <= 5
         assert abs(best.nu_pre - best.nu_post) <= 1
         back = np.empty((n, n, n))
         mg.mg_get_field(g, 0, -1, back)
