@@ -179,6 +179,8 @@ _KERNEL_SOURCES = {
                            "int tpb_for(long long items)", "void launch_smooth64(")),
     "k_smooth_colour32_n": (("mg_bodies32.cuh", "mg_common.cuh"), "mg_mixed.cu",
                             ("__global__ void __launch_bounds__(256) k_smooth_colour32_n(",
+                             "__device__ __forceinline__ long long colour_cell(",
+                             "static void launch_colour32_n(",
                              "  void smooth(int l, int sweeps) const {")),
     "k_smooth_slab32": (("mg_bodies32.cuh", "mg_common.cuh"), "mg_mixed.cu",
                         ("__global__ void __launch_bounds__(256) k_smooth_slab32(",
@@ -204,17 +206,19 @@ def kernel_source_hash(kernel: str = "k_smooth_colour64"):
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(kernel: str, cells_per_launch: float):
+def traffic_per_launch(kernel: str, cells_per_launch: float, **launch):
     """DRAM bytes per launch of `kernel` at `cells_per_launch` cell updates, from the
-    committed ncu record, if it was taken on the current kernel source (else None).
-    The record was taken on a grid whose arrays exceed L2, so the traffic grows in
-    proportion to the cells a launch updates."""
+    committed ncu record, if it was taken on the current kernel source and with the
+    launch parameters given (for instance tile32=4), else None.  The record was taken
+    on a grid whose arrays exceed L2, so the traffic grows in proportion to the cells
+    a launch updates."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     ent = json.load(open(path)).get(kernel)
     if (not ent or ent.get("source_hash") != kernel_source_hash(kernel) or
-            not ent.get("bytes_per_launch") or not ent.get("cells_per_launch")):
+            not ent.get("bytes_per_launch") or not ent.get("cells_per_launch") or
+            any(ent.get(k) != v for k, v in launch.items())):
         return None
     return ent["bytes_per_launch"] * cells_per_launch / ent["cells_per_launch"]
 
@@ -296,7 +300,8 @@ def run_ours(args):
                                      use_cache=False)
         tuned["fp64" if prec == mg.MG_FP64 else "mixed"] = {
             "nu_pre": best.nu_pre, "nu_post": best.nu_post, "inner_cycles": best.inner_cycles,
-            "half32": best.half32, "slab32": best.slab32, "tune_s": time.perf_counter() - t0}
+            "half32": best.half32, "slab32": best.slab32, "tile32": best.tile32,
+            "tune_s": time.perf_counter() - t0}
         return g, best
 
     g64, best64 = tune(mg.MG_FP64)
@@ -333,7 +338,8 @@ def run_ours(args):
     ach32 = BYTES_PER_CELL_FP32 * cells32 / avg32 / 1e9
     slab = bestmx.slab32 if (not bestmx.half32 and N >= 256 and N % max(bestmx.slab32, 1) == 0) else 0
     k32 = "k_half32" if bestmx.half32 else "k_smooth_slab32" if slab else "k_smooth_colour32_n"
-    traffic32 = traffic_per_launch(k32, cells32)
+    traffic32 = (traffic_per_launch(k32, cells32, tile32=bestmx.tile32)
+                 if k32 == "k_smooth_colour32_n" else traffic_per_launch(k32, cells32))
     # FP64 smoother, bound by the FP64 pipe
     avg64, cells64, n64 = kernel_rate(stats)
     ach64 = FLOP_PER_CELL_FP64 * cells64 / avg64 / 1e12
@@ -343,6 +349,8 @@ def run_ours(args):
         "kernel": (f"k_half32<{N}> (finest FP32 half sweep, two colours, mixed)" if bestmx.half32
                    else f"k_smooth_slab32<{N}> (finest FP32 sweep in slabs of {slab} planes, "
                         f"{4 * N // max(slab, 1)} launches; one timed unit is a whole sweep)" if slab
+                   else f"k_smooth_colour32_n<{N}> (finest FP32 colour stage, mixed; CTA tile "
+                        f"32 x {8 // bestmx.tile32} rows x {bestmx.tile32} planes)" if bestmx.tile32
                    else f"k_smooth_colour32_n<{N}> (finest FP32 colour stage, mixed)"),
         "achieved": ach32, "peak": hbm_peak, "unit": "GB/s", "frac": ach32 / hbm_peak,
         "traffic": traffic32, "peak_source": peak_src,

@@ -155,6 +155,11 @@ typedef struct {
                         it reads in L2 (same arithmetic, same bits as whole colour
                         stages); one of 0 (whole colour stages, default), 8, 16, 32, 64,
                         128, 256. */
+  int tile32;        /* mixed precision, levels with n >= 64 (a power of two): the cells a
+                        256-thread CTA of an FP32 colour stage updates, a tile of 32 cells
+                        in x by 8 / tile32 rows of the colour by tile32 planes (1, 2, 4 or
+                        8; default 4), so that the rows around its cells overlap in L1; 0
+                        takes 256 consecutive cells.  Same bits whatever the shape. */
 } mg_options;
 
 typedef struct {
@@ -262,8 +267,9 @@ mg_status mg_set_options(mg_grid* g, const mg_options* opt);
  * pair (nu_pre, nu_post) from {1,1 2,1 1,2 2,2 3,2 2,3 3,3 4,3 3,4 4,4 5,4 4,5
  * 5,5}, for MG_MIXED inner_cycles in {3,4}, and for n <= 64 fuse_coarse in
  * {0,1}.  For MG_MIXED with n >= 256 it then tries, at the winning counts, the
- * shapes of the FP32 sweep: whole colour stages, slabs of slab32 in {8,16,32,64}
- * planes, and (n = 256 or 512) half32 = 1.  Each candidate is solved and timed
+ * shapes of the FP32 sweep: whole colour stages with CTA tiles of tile32 in
+ * {0,1,2,4,8} planes, slabs of slab32 in {8,16,32,64} planes, and (n = 256 or
+ * 512) half32 = 1.  Each candidate is solved and timed
  * on the device (twice for n <= 64, where the second solve counts).  The fastest
  * candidate that converges to
  * `tol` becomes the handle's options and is returned in *best (may be NULL) with

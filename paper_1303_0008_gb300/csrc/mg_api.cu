@@ -55,6 +55,7 @@ void mg_default_options(mg_options* opt) {
   opt->half32 = 0;
   opt->barrier_timeout_s = 1.0;
   opt->slab32 = 0;
+  opt->tile32 = 4;
 }
 
 static mg_status check_options(const mg_options& o) {
@@ -86,6 +87,8 @@ static mg_status check_options(const mg_options& o) {
     MG_FAIL(MG_EINVAL, "options: barrier_timeout_s must be in [0, 3600]");
   if (o.slab32 != 0 && !(o.slab32 >= 8 && o.slab32 <= 256 && (o.slab32 & (o.slab32 - 1)) == 0))
     MG_FAIL(MG_EINVAL, "options: slab32 must be 0 or a power of two from 8 to 256");
+  if (o.tile32 != 0 && o.tile32 != 1 && o.tile32 != 2 && o.tile32 != 4 && o.tile32 != 8)
+    MG_FAIL(MG_EINVAL, "options: tile32 must be 0, 1, 2, 4 or 8");
   return MG_OK;
 }
 

@@ -1,6 +1,7 @@
 // Autotuner: pick the sweep counts (and, for the mixed path, the inner V-cycles
-// per FP64 correction and the shape of the FP32 sweep: four colour launches, slabs
-// of z planes in a staggered order, or two half sweeps over tiles of whole rows)
+// per FP64 correction and the shape of the FP32 sweep: four colour launches with
+// their CTA tile, slabs of z planes in a staggered order, or two half sweeps over
+// tiles of whole rows)
 // that give the shortest time to the
 // requested residual on the handle's own problem, and remember the choice in a
 // small JSON file keyed by grid size, precision and device name.
@@ -127,6 +128,7 @@ extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double ka
     o.fuse_coarse = (int)e.at("fuse_coarse");
     if (e.count("half32")) o.half32 = (int)e.at("half32");
     if (e.count("slab32")) o.slab32 = (int)e.at("slab32");
+    if (e.count("tile32")) o.tile32 = (int)e.at("tile32");
     g->opt = o;
     if (best) *best = o;
     if (best_seconds) *best_seconds = e.count("seconds") ? e.at("seconds") : -1.0;
@@ -195,7 +197,11 @@ extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double ka
     o.sweep32 = 0;
     o.pair32 = 0;
     o.slab32 = 0;
-    shapes.push_back(o);
+    for (int tz : {0, 1, 2, 4, 8}) {
+      o.tile32 = tz;
+      shapes.push_back(o);
+    }
+    o.tile32 = first.tile32;
     for (int S : {8, 16, 32, 64})
       if (slab_sweep_applies(d->n, S)) {
         o.slab32 = S;
@@ -208,7 +214,7 @@ extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double ka
     }
     for (const mg_options& c : shapes)
       if (c.half32 != first.half32 || c.slab32 != first.slab32 || c.sweep32 != first.sweep32 ||
-          c.pair32 != first.pair32)
+          c.pair32 != first.pair32 || c.tile32 != first.tile32)
         trial(c);
   }
   cudaMemcpyAsync(d->lv[0].phi, saved, bytes, cudaMemcpyDeviceToDevice, g->stream);
@@ -228,6 +234,7 @@ extern "C" mg_status mg_autotune(mg_grid* g, int branch, double alpha, double ka
                   {"fuse_coarse", (double)o_best.fuse_coarse},
                   {"half32", (double)o_best.half32},
                   {"slab32", (double)o_best.slab32},
+                  {"tile32", (double)o_best.tile32},
                   {"seconds", t_best}};
     if (!write_cache(cache_path, cache)) {
       set_error("mg_autotune: cannot write the cache file");

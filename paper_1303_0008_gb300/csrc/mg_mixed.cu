@@ -84,11 +84,31 @@ __global__ void __launch_bounds__(256) k_smooth_colour32(int n, float* __restric
   b_smooth_colour32(n, e, phi0, q0, g, sc, c, colour, blockIdx.x);
 }
 
+constexpr int ilog2(unsigned v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+
+// Which of a colour's N^3/4 cells thread tid of a 256-thread CTA blk updates.
+// tzl < 0: consecutive cells (a CTA covers 256 cells of one or a few rows of the
+// colour).  tzl = 0..3: a CTA covers a tile of 32 cells in x by 8 / 2^tzl rows of the
+// colour by 2^tzl planes, so that the rows its warps read around their cells
+// overlap inside the CTA and its L1.  Each warp holds 32 consecutive cells of one
+// row either way, and every cell is updated once.
+template <int N, int TZL>
+__device__ __forceinline__ long long colour_cell(unsigned blk, unsigned tid) {
+  if (TZL < 0) return (long long)blk * 256 + tid;
+  constexpr unsigned HN = N / 2, BX = HN / 32;
+  constexpr unsigned tzl = TZL < 0 ? 0 : TZL, tyl = 3 - tzl, byl = ilog2(HN) - tyl;
+  const unsigned w = tid >> 5, r = blk / BX;
+  const unsigned m = (blk % BX) * 32 + (tid & 31);
+  const unsigned jj = ((r & ((1u << byl) - 1)) << tyl) + (w & ((1u << tyl) - 1));
+  const unsigned k = ((r >> byl) << tzl) + (w >> tyl);
+  return ((long long)k * HN + jj) * HN + m;
+}
+
 // The same colour stage for a power-of-two side N >= 64 known at compile time
 // (immediate neighbour offsets; cell_smooth32_n).
 // CO: q0 and g in colour order (the finest level, where the hand-off writes them
-// so), the pointers already at this colour's block.
-template <int N, bool CO>
+// so), the pointers already at this colour's block.  TZL: the CTA tile (colour_cell).
+template <int N, bool CO, int TZL>
 __global__ void __launch_bounds__(256) k_smooth_colour32_n(float* __restrict__ e,
                                                            const float* __restrict__ phi0,
                                                            const float* __restrict__ q0,
@@ -100,7 +120,21 @@ __global__ void __launch_bounds__(256) k_smooth_colour32_n(float* __restrict__ e
   if (threadIdx.x == 0) s_mu = (float)sc->lambda;
   __syncthreads();
   cell_smooth32_n<N, CO>(e, phi0, q0, g, s_mu, c, colour,
-                         (long long)blockIdx.x * blockDim.x + threadIdx.x);
+                         colour_cell<N, TZL>(blockIdx.x, threadIdx.x));
+}
+
+// One colour stage of k_smooth_colour32_n with the CTA tile tzl (-1 .. 3).
+template <int N, bool CO>
+static void launch_colour32_n(cudaStream_t st, int tzl, unsigned nb, float* e, const float* phi0,
+                              const float* q0, const float* g, const LevelScalars* sc,
+                              const OpConst32& c, int colour) {
+  switch (tzl) {
+    case 0: launch_k(k_smooth_colour32_n<N, CO, 0>, nb, 256, 0, st, e, phi0, q0, g, sc, c, colour); break;
+    case 1: launch_k(k_smooth_colour32_n<N, CO, 1>, nb, 256, 0, st, e, phi0, q0, g, sc, c, colour); break;
+    case 2: launch_k(k_smooth_colour32_n<N, CO, 2>, nb, 256, 0, st, e, phi0, q0, g, sc, c, colour); break;
+    case 3: launch_k(k_smooth_colour32_n<N, CO, 3>, nb, 256, 0, st, e, phi0, q0, g, sc, c, colour); break;
+    default: launch_k(k_smooth_colour32_n<N, CO, -1>, nb, 256, 0, st, e, phi0, q0, g, sc, c, colour);
+  }
 }
 
 // The colour stage of k_smooth_colour32_n on the planes z0, ..., z0 + nz - 1 (mod
@@ -339,6 +373,8 @@ struct CycleMixed {
       slab_sweeps(l, sweeps, co, t);
       return;
     }
+    // CTA tiles of tile32 planes (log2; -1: consecutive cells)
+    const int tzl = o->tile32 > 0 ? ilog2((unsigned)o->tile32) : -1;
     for (int s = 0; s < sweeps; ++s)
       for (int colour = 0; colour < 4; ++colour) {
         const unsigned nb = nblk(per, 256);
@@ -348,25 +384,15 @@ struct CycleMixed {
         if (timed) t->begin(st);
         const float* qv = co ? L.q0c + colour * per : L.q0;
         const float* gv = co ? L.rhsc + colour * per : L.rhs;
-        auto stage = [&](auto kern) {
-          launch_k(kern, nb, 256, 0, st, L.e, L.phi0, qv, gv, sc32(l), ops32[l], colour);
+        auto stage = [&](auto launch_co, auto launch_nat) {
+          (co ? launch_co : launch_nat)(st, tzl, nb, L.e, L.phi0, qv, gv, sc32(l), ops32[l], colour);
         };
         switch (L.n) {
-          case 64:
-            co ? stage(k_smooth_colour32_n<64, true>) : stage(k_smooth_colour32_n<64, false>);
-            break;
-          case 128:
-            co ? stage(k_smooth_colour32_n<128, true>) : stage(k_smooth_colour32_n<128, false>);
-            break;
-          case 256:
-            co ? stage(k_smooth_colour32_n<256, true>) : stage(k_smooth_colour32_n<256, false>);
-            break;
-          case 512:
-            co ? stage(k_smooth_colour32_n<512, true>) : stage(k_smooth_colour32_n<512, false>);
-            break;
-          case 1024:
-            co ? stage(k_smooth_colour32_n<1024, true>) : stage(k_smooth_colour32_n<1024, false>);
-            break;
+          case 64: stage(launch_colour32_n<64, true>, launch_colour32_n<64, false>); break;
+          case 128: stage(launch_colour32_n<128, true>, launch_colour32_n<128, false>); break;
+          case 256: stage(launch_colour32_n<256, true>, launch_colour32_n<256, false>); break;
+          case 512: stage(launch_colour32_n<512, true>, launch_colour32_n<512, false>); break;
+          case 1024: stage(launch_colour32_n<1024, true>, launch_colour32_n<1024, false>); break;
           default:
             launch_k(k_smooth_colour32, nb, 256, 0, st, L.n, L.e, L.phi0, L.q0, L.rhs, sc32(l),
                      ops32[l], colour);

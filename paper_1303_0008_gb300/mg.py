@@ -41,7 +41,8 @@ class mg_options(ctypes.Structure):
                 ("sweep32", ctypes.c_int), ("pair32", ctypes.c_int),
                 ("tau_stop", ctypes.c_double), ("w", ctypes.c_double),
                 ("patch_galerkin", ctypes.c_int), ("half32", ctypes.c_int),
-                ("barrier_timeout_s", ctypes.c_double), ("slab32", ctypes.c_int)]
+                ("barrier_timeout_s", ctypes.c_double), ("slab32", ctypes.c_int),
+                ("tile32", ctypes.c_int)]
 
 
 class mg_solve_stats(ctypes.Structure):

@@ -104,3 +104,10 @@ def test_slab_option_is_validated_without_gpu(bad):
     with pytest.raises(mg.MGError) as e:
         mg.mg_create_grid(64, mg.options(prec=mg.MG_MIXED, slab32=bad))
     assert e.value.status == mg.MG_EINVAL
+
+
+@pytest.mark.parametrize("bad", [3, 16, -1])
+def test_tile_option_is_validated_without_gpu(bad):
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_create_grid(64, mg.options(prec=mg.MG_MIXED, tile32=bad))
+    assert e.value.status == mg.MG_EINVAL
