@@ -216,8 +216,14 @@ def traffic_per_launch(kernel: str, cells_per_launch: float, **launch):
     if not os.path.exists(path):
         return None
     ent = json.load(open(path)).get(kernel)
-    if (not ent or ent.get("source_hash") != kernel_source_hash(kernel) or
-            not ent.get("bytes_per_launch") or not ent.get("cells_per_launch") or
+    if not ent or ent.get("source_hash") != kernel_source_hash(kernel):
+        return None
+    # records taken at several launch shapes: {"by_tile32": {"4": {...}, ...}}
+    for k, v in launch.items():
+        sub = ent.get("by_" + k)
+        if sub is not None:
+            ent = dict(ent, **sub.get(str(v), {"bytes_per_launch": None}), **{k: v})
+    if (not ent.get("bytes_per_launch") or not ent.get("cells_per_launch") or
             any(ent.get(k) != v for k, v in launch.items())):
         return None
     return ent["bytes_per_launch"] * cells_per_launch / ent["cells_per_launch"]
@@ -392,11 +398,23 @@ def run_ours(args):
     ge = mg.mg_create_grid(N, mg.options(nu_pre=best64.nu_pre, nu_post=best64.nu_post))
     mg.mg_set_stream(ge, stream)
 
-    def e2e_step():
+    phases = {"set_density": 0.0, "set_field": 0.0, "solve": 0.0, "get_field": 0.0}
+
+    def e2e_step(acc=None):
+        # each call returns after its work is done (the copies synchronise the
+        # stream, the solve reads its residuals back), so host stamps split the step
+        t = [time.perf_counter()]
         mg.mg_set_density(ge, 0, -1, host_delta)
+        t.append(time.perf_counter())
         mg.mg_set_field(ge, 0, -1, host_zero)
+        t.append(time.perf_counter())
         mg.mg_solve(ge, w["branch"], w["alpha"], w["kappa"], TOL)
+        t.append(time.perf_counter())
         mg.mg_get_field(ge, 0, -1, host_out)
+        t.append(time.perf_counter())
+        if acc is not None:
+            for name, a, b in zip(acc, t, t[1:]):
+                acc[name] += (b - a) * 1e3
 
     for _ in range(args.warmup):
         e2e_step()
@@ -407,7 +425,7 @@ def run_ours(args):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            e2e_step()
+            e2e_step(phases)
             torch.cuda.synchronize()
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     barrier()
@@ -416,7 +434,8 @@ def run_ours(args):
     cell_bytes = delta_np.size * 8
     e2e = {"value": solves_done / (e2e_total * 1e-3), "unit": "solves/s",
            "h2d_bytes_per_step": 2 * cell_bytes, "d2h_bytes_per_step": cell_bytes,
-           "ms_per_step": e2e_total / args.steps, "clocks": clk_e2e.summary()}
+           "ms_per_step": e2e_total / args.steps, "clocks": clk_e2e.summary(),
+           "phase_ms_per_step": {k: v / args.steps for k, v in phases.items()}}
 
     s0, m0 = stats[0], stats_m[0]
     line = {

@@ -63,9 +63,15 @@ def test_traffic_record_matches_the_smoother_source(kernel):
         assert part.startswith(head) and part.rstrip().endswith("}")
     rec = json.load(open(os.path.join(root, "profiles", "traffic.json")))[kernel]
     assert rec["source_hash"] == bench.kernel_source_hash(kernel)
-    full = bench.traffic_per_launch(kernel, 2 * rec["cells_per_launch"],
-                                    **({"tile32": rec["tile32"]} if "tile32" in rec else {}))
-    assert full == 2 * rec["bytes_per_launch"] > 0
+    shapes = rec.get("by_tile32")
+    if shapes:
+        for tile, sub in shapes.items():
+            full = bench.traffic_per_launch(kernel, 2 * rec["cells_per_launch"], tile32=int(tile))
+            assert full == 2 * sub["bytes_per_launch"] > 0
+        assert bench.traffic_per_launch(kernel, rec["cells_per_launch"], tile32=3) is None
+    else:
+        full = bench.traffic_per_launch(kernel, 2 * rec["cells_per_launch"])
+        assert full == 2 * rec["bytes_per_launch"] > 0
 
 
 def test_reference_arm_prints_one_line(capsys, monkeypatch):
