@@ -223,28 +223,55 @@ __device__ __forceinline__ void cell_smooth32(int n, float* __restrict__ e,
   cell_smooth32_at(n, e, phi0, q0[id], g[id], mu, c, i, j, k, id);
 }
 
-// Face sums and cross differences around c0 for a side N known at compile time and
-// a cell off the y and z boundaries: cxp / cxm point at the x neighbours (the x
-// wrap is folded into them), so every load is a base pointer plus an immediate.
-// The sums are those of gather_at in the same order.
-template <int N>
-__device__ __forceinline__ StencilT<float> gather_n(const float* c0, const float* cxp,
-                                                    const float* cxm) {
+// Face sums and cross differences around the cell at c0, for a side N known at
+// compile time and a cell off the y and z boundaries, with 8-byte loads of
+// x-adjacent pairs.  A warp's cells of one colour sit at every other x of one row,
+// all with the x parity P, so in each row that the stencil reads at x - 1, x and
+// x + 1 two aligned pairs hold all three values:
+//   P = 0: (x-2, x-1) and (x, x+1);   P = 1: (x-1, x) and (x+1, x+2).
+// lo / hi are the offsets of those pairs from the cell (the x wrap folded in: the
+// pair holding x - 1 of x = 0 is (N-2, N-1), the pair holding x + 1 of x = N - 1 is
+// (0, 1)).  The centre row, the two y rows and the two z rows take two pair loads
+// each and the four yz rows one scalar load: 14 loads instead of 18, with the same
+// sums in the same order as gather_at.
+template <int N, int P>
+__device__ __forceinline__ StencilT<float> gather_n2(const float* c0, int lo, int hi) {
   constexpr int Y = N, Z = N * N;
+  auto pair = [&](int off) { return *reinterpret_cast<const float2*>(c0 + off); };
+  // x - 1, x, x + 1 of the row at offset r
+  auto row = [&](int r, float& vm, float& v0, float& vp) {
+    const float2 a = pair(lo + r), b = pair(hi + r);
+    if (P == 0) {
+      vm = a.y;
+      v0 = b.x;
+      vp = b.y;
+    } else {
+      vm = a.x;
+      v0 = a.y;
+      vp = b.x;
+    }
+  };
+  float cm, c_, cp, ypm, yp0, ypp, ymm, ym0, ymp, zpm, zp0, zpp, zmm, zm0, zmp;
+  row(0, cm, c_, cp);
+  row(Y, ypm, yp0, ypp);
+  row(-Y, ymm, ym0, ymp);
+  row(Z, zpm, zp0, zpp);
+  row(-Z, zmm, zm0, zmp);
   StencilT<float> s;
-  s.sx = cxp[0] + cxm[0];
-  s.sy = c0[Y] + c0[-Y];
-  s.sz = c0[Z] + c0[-Z];
-  s.cxy = (cxp[Y] + cxm[-Y]) - (cxp[-Y] + cxm[Y]);
-  s.cxz = (cxp[Z] + cxm[-Z]) - (cxp[-Z] + cxm[Z]);
+  s.sx = cp + cm;
+  s.sy = yp0 + ym0;
+  s.sz = zp0 + zm0;
+  s.cxy = (ypp + ymm) - (ymp + ypm);
+  s.cxz = (zpp + zmm) - (zmp + zpm);
   s.cyz = (c0[Y + Z] + c0[-Y - Z]) - (c0[Y - Z] + c0[-Y + Z]);
   return s;
 }
 
 // cell_smooth32 for a side N known at compile time (N >= 64, so that a warp's 32
 // cells share their row, and the y/z-boundary test below is uniform per warp).
-// Rows on a y or z boundary take the general path; the others address their
-// neighbours with immediates.  The arithmetic is cell_smooth32's, so the bits are.
+// Rows on a y or z boundary take the general path; the others read their
+// neighbours as pairs at immediate offsets (gather_n2).  The arithmetic is
+// cell_smooth32's, so the bits are.
 // With CO, q0 and g arrive in colour order (colour_index): q0 and g point at this
 // colour's block, whose entry t is the cell the thread with index t updates, so a
 // warp reads them contiguously; otherwise they are the natural n^3 arrays.
@@ -268,14 +295,20 @@ __device__ __forceinline__ void cell_smooth32_n(float* __restrict__ e,
     cell_smooth32_at(N, e, phi0, q0v, gv, mu, c, i, j, k, id);
     return;
   }
-  const int xp = (i == N - 1) ? 1 - N : 1, xm = (i == 0) ? N - 1 : -1;
-  const float* ce = e + id;
-  const StencilT<float> se = gather_n<N>(ce, ce + xp, ce + xm);
-  float dd = 0.f;
-  if (!c.linear) {
-    const float* cp = phi0 + id;
-    dd = dD32(se, gather_n<N>(cp, cp + xp, cp + xm), q0v, c);
+  // pair offsets (gather_n2); the x parity is uniform over the warp
+  const int par = i & 1;
+  const int lo = par ? -1 : (i == 0 ? N - 2 : -2);
+  const int hi = par ? (i == N - 1 ? 1 - N : 1) : 0;
+  const float *ce = e + id, *cp = phi0 + id;
+  StencilT<float> se, sp;
+  if (par) {
+    se = gather_n2<N, 1>(ce, lo, hi);
+    if (!c.linear) sp = gather_n2<N, 1>(cp, lo, hi);
+  } else {
+    se = gather_n2<N, 0>(ce, lo, hi);
+    if (!c.linear) sp = gather_n2<N, 0>(cp, lo, hi);
   }
+  const float dd = c.linear ? 0.f : dD32(se, sp, q0v, c);
   e[id] = gs_value32(se, dd, gv, mu, c);
 }
 
