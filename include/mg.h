@@ -159,7 +159,9 @@ typedef struct {
                         256-thread CTA of an FP32 colour stage updates, a tile of 32 cells
                         in x by 8 / tile32 rows of the colour by tile32 planes (1, 2, 4 or
                         8; default 4), so that the rows around its cells overlap in L1; 0
-                        takes 256 consecutive cells.  Same bits whatever the shape. */
+                        takes 256 consecutive cells.  From n = 256 on, where each thread
+                        updates two cells on planes k and k + 2, the tile counts such pairs
+                        of planes.  Same bits whatever the shape. */
 } mg_options;
 
 typedef struct {

@@ -267,6 +267,55 @@ __device__ __forceinline__ StencilT<float> gather_n2(const float* c0, int lo, in
   return s;
 }
 
+// gather_n2 for two cells of one colour at the same x and y on planes k (at c0) and
+// k + 2 (the parities repeat every two planes): the row (j, k+1) is the z + 1 row of
+// the first cell and the z - 1 row of the second, and the yz rows (j±1, k+1) are
+// shared the same way, so the two stencils take 24 loads instead of 28.  The sums
+// are gather_n2's, in the same order.
+template <int N, int P>
+__device__ __forceinline__ void gather_n2_z2(const float* c0, int lo, int hi,
+                                             StencilT<float>& sa, StencilT<float>& sb) {
+  constexpr int Y = N, Z = N * N;
+  auto pair = [&](int off) { return *reinterpret_cast<const float2*>(c0 + off); };
+  auto row = [&](int r, float& vm, float& v0, float& vp) {
+    const float2 a = pair(lo + r), b = pair(hi + r);
+    if (P == 0) {
+      vm = a.y;
+      v0 = b.x;
+      vp = b.y;
+    } else {
+      vm = a.x;
+      v0 = a.y;
+      vp = b.x;
+    }
+  };
+  float am, a0, ap, aypm, ayp0, aypp, aymm, aym0, aymp, azmm, azm0, azmp;
+  float sm, s0, sp;  // the shared row (j, k+1)
+  float bm, b0, bp, bypm, byp0, bypp, bymm, bym0, bymp, bzpm, bzp0, bzpp;
+  row(0, am, a0, ap);
+  row(Y, aypm, ayp0, aypp);
+  row(-Y, aymm, aym0, aymp);
+  row(-Z, azmm, azm0, azmp);
+  row(Z, sm, s0, sp);
+  row(2 * Z, bm, b0, bp);
+  row(2 * Z + Y, bypm, byp0, bypp);
+  row(2 * Z - Y, bymm, bym0, bymp);
+  row(3 * Z, bzpm, bzp0, bzpp);
+  const float dyp = c0[Y + Z], dym = c0[-Y + Z];  // the shared yz cells (j±1, k+1)
+  sa.sx = ap + am;
+  sa.sy = ayp0 + aym0;
+  sa.sz = s0 + azm0;
+  sa.cxy = (aypp + aymm) - (aymp + aypm);
+  sa.cxz = (sp + azmm) - (azmp + sm);
+  sa.cyz = (dyp + c0[-Y - Z]) - (c0[Y - Z] + dym);
+  sb.sx = bp + bm;
+  sb.sy = byp0 + bym0;
+  sb.sz = bzp0 + s0;
+  sb.cxy = (bypp + bymm) - (bymp + bypm);
+  sb.cxz = (bzpp + sm) - (sp + bzpm);
+  sb.cyz = (c0[Y + 3 * Z] + dym) - (dyp + c0[-Y + 3 * Z]);
+}
+
 // cell_smooth32 for a side N known at compile time (N >= 64, so that a warp's 32
 // cells share their row, and the y/z-boundary test below is uniform per warp).
 // Rows on a y or z boundary take the general path; the others read their
@@ -310,6 +359,51 @@ __device__ __forceinline__ void cell_smooth32_n(float* __restrict__ e,
   }
   const float dd = c.linear ? 0.f : dD32(se, sp, q0v, c);
   e[id] = gs_value32(se, dd, gv, mu, c);
+}
+
+// Two cells of one colour stage per thread (cell_smooth32_n on each, sharing the
+// rows between them): tp < N^3/8 indexes pairs of planes, the plane pair kp holding
+// the planes k = 4 (kp / 2) + kp % 2 and k + 2, so that every plane is covered once.
+// A pair with a cell on a y or z boundary runs cell_smooth32_n on each cell.
+template <int N, bool CO>
+__device__ __forceinline__ void cell_smooth32_n_z2(float* __restrict__ e,
+                                                   const float* __restrict__ phi0,
+                                                   const float* __restrict__ q0,
+                                                   const float* __restrict__ g, float mu,
+                                                   const OpConst32& c, int colour, long long tp) {
+  constexpr int HN = N / 2;
+  constexpr long long HH = (long long)HN * HN;
+  if (tp >= HH * (N / 2)) return;
+  const unsigned u = (unsigned)tp;
+  const int m = (int)(u % HN), jj = (int)((u / HN) % HN), kp = (int)(u / (HN * HN));
+  const int k = 4 * (kp >> 1) + (kp & 1);
+  const long long ta = ((long long)k * HN + jj) * HN + m, tb = ta + 2 * HH;
+  const int i = 2 * m + ((colour ^ k) & 1);
+  const int j = 2 * jj + (((colour >> 1) ^ k) & 1);
+  if (j == 0 || j == N - 1 || k == 0 || k + 2 == N - 1) {
+    cell_smooth32_n<N, CO>(e, phi0, q0, g, mu, c, colour, ta);
+    cell_smooth32_n<N, CO>(e, phi0, q0, g, mu, c, colour, tb);
+    return;
+  }
+  const long long ida = (long long)i + (long long)N * (j + (long long)N * k);
+  const long long idb = ida + 2LL * N * N;
+  const float qa = CO ? q0[ta] : q0[ida], qb = CO ? q0[tb] : q0[idb];
+  const float ga = CO ? g[ta] : g[ida], gb = CO ? g[tb] : g[idb];
+  const int par = i & 1;
+  const int lo = par ? -1 : (i == 0 ? N - 2 : -2);
+  const int hi = par ? (i == N - 1 ? 1 - N : 1) : 0;
+  StencilT<float> sea, seb, spa, spb;
+  if (par) {
+    gather_n2_z2<N, 1>(e + ida, lo, hi, sea, seb);
+    if (!c.linear) gather_n2_z2<N, 1>(phi0 + ida, lo, hi, spa, spb);
+  } else {
+    gather_n2_z2<N, 0>(e + ida, lo, hi, sea, seb);
+    if (!c.linear) gather_n2_z2<N, 0>(phi0 + ida, lo, hi, spa, spb);
+  }
+  const float dda = c.linear ? 0.f : dD32(sea, spa, qa, c);
+  const float ddb = c.linear ? 0.f : dD32(seb, spb, qb, c);
+  e[ida] = gs_value32(sea, dda, ga, mu, c);
+  e[idb] = gs_value32(seb, ddb, gb, mu, c);
 }
 
 __device__ __forceinline__ void b_smooth_colour32(int n, float* __restrict__ e,
