@@ -227,6 +227,21 @@ __global__ void __launch_bounds__(256) k_prolong_correct32(int nc, const float* 
   b_prolong_correct32(nc, e_c, ehat_c, e_f, blockIdx.x);
 }
 
+// ehat_c <- e_c - ehat_c (R e is not needed after the prolongation), then the
+// prolongation from it (as k_correction64 and k_prolong_corr64).
+__global__ void __launch_bounds__(256) k_correction32(long long cells, const float* __restrict__ e_c,
+                                                      float* __restrict__ ehat_c) {
+  PdlScope pdl_scope;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < cells) ehat_c[t] = e_c[t] - ehat_c[t];
+}
+
+__global__ void __launch_bounds__(256) k_prolong_corr32(int nc, const float* __restrict__ corr_c,
+                                                        float* __restrict__ e_f) {
+  PdlScope pdl_scope;
+  cell_prolong_corr32(nc, corr_c, e_f, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // Coarsest inner level in one CTA, in FP32: sweeps of N(e) = g + mu until the
 // residual fell by `drop` or `max_sweeps`.
 __global__ void __launch_bounds__(256) k_coarsest_corr32(int n, float* __restrict__ e,
@@ -499,7 +514,13 @@ struct CycleMixed {
     launch_k(k_fas_rhs32, nblk(C.cells, 256), 256, 0, st, C.n, C.e, C.phi0, C.q0, C.rhs, ops32[l + 1],
                                                      sc32(l), sc32(l + 1));
     inner(l + 1);
-    launch_k(k_prolong_correct32, nblk(L.cells, 256), 256, 0, st, C.n, C.e, C.ehat, L.e);
+    if (L.cells >= kCorrectionMinFine) {
+      launch_k(k_correction32, nblk(C.cells, 256), 256, 0, st, C.cells, C.e, C.ehat);
+      launch_k(k_prolong_corr32, nblk(L.cells, 256), 256, 0, st, C.n, (const float*)C.ehat, L.e);
+      count_launches(1);
+    } else {
+      launch_k(k_prolong_correct32, nblk(L.cells, 256), 256, 0, st, C.n, C.e, C.ehat, L.e);
+    }
     count_launches(3);  // residual-restrict, FAS right-hand side, prolongation
     smooth(l, o->nu_post);
   }
