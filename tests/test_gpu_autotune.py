@@ -49,3 +49,32 @@ def test_autotune_picks_caches_and_restores(tmp_path, prec):
         mg.mg_destroy_grid(g)
     ref, _ = O.fas_solve(delta, a, 1.0, tol=1e-12)
     assert np.abs(phi - ref).max() / np.abs(ref).max() < 1e-10
+
+
+def test_autotune_tries_the_fp32_sweep_shapes_at_256(tmp_path):
+    """From n = 256 the mixed tuner's second stage times the FP32 sweep shapes (CTA
+    tiles, slabs, half sweeps) at the first stage's counts; the choice is a valid
+    shape, is cached with the counts, and the solve it gives meets the tolerance."""
+    n = 256
+    delta = torch.from_numpy(I.lognormal_delta(n, 1.5, 1340)).cuda()
+    a = I.alpha_kappa_for_rv(8.0)
+    cache = str(tmp_path / "tune256.json")
+    g = mg.mg_create_grid(n, mg.options(prec=mg.MG_MIXED))
+    try:
+        mg.mg_set_density(g, 0, -1, delta)
+        best, t = mg.mg_autotune(g, 0, a, 1.0, 1e-8, cache, use_cache=False)
+        assert t > 0
+        assert best.tile32 in (0, 1, 2, 4, 8)
+        assert best.slab32 in (0, 8, 16, 32, 64)
+        assert best.half32 in (0, 1)
+        assert not (best.half32 and best.slab32)
+        entry = list(json.load(open(cache)).values())[0]
+        for k in ("nu_pre", "nu_post", "inner_cycles", "half32", "slab32", "tile32"):
+            assert entry[k] == getattr(best, k), k
+        again, _ = mg.mg_autotune(g, 0, a, 1.0, 1e-8, cache, use_cache=True)
+        assert mg.options_dict(again) == mg.options_dict(best)
+        mg.mg_set_field(g, 0, -1, torch.zeros_like(delta))
+        st = mg.mg_solve(g, 0, a, 1.0, 1e-8)
+        assert st["rc"] == mg.MG_OK and st["res"] < 1e-8
+    finally:
+        mg.mg_destroy_grid(g)
